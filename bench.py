@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the blocked 3D acoustic stencil sweep on GB300.
+
+Workload: one seismic shot on a 512^3 FP32 grid, layered velocity model of 8
+horizontal layers with velocities drawn uniform in [1500, 4500) m/s
+(seed 1310), dx = 10 m, dt = 0.5 x the CFL bound for the largest velocity,
+15 Hz Ricker source at the grid centre, ghost-zero boundaries, 10th-order
+space / 2nd-order time stencil (R = 5; --radius 4 for 8th order), 200 time
+steps.  One benchmark "step" = one whole shot (reset the wavefields, 200
+sweeps); the velocity model, kappa and the tile are set up once, outside the
+timed region.  Every array (3 x 512 MiB) is larger than L2, so no L2 flush is
+needed between iterations.
+
+Metric: grid-point updates per second (nx*ny*nz*timesteps / time), reported
+in GPt-updates/s, with the dominant kernel's achieved HBM bandwidth at the
+algorithmic 16 B per point update (read u, u_prev, kappa; write u_next in
+place) against the measured HBM copy bandwidth.
+
+Prints exactly one JSON line (rank 0).  --impl reference times the FP64 CPU
+oracle on this host's cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GPt-updates/s"
+BYTES_PER_POINT = 16            # algorithmic minimum, FP32: u, u_prev, kappa read; u_next written
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5, help="timed shots")
+    ap.add_argument("--warmup", type=int, default=3, help="untimed shots")
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512, help="cube side")
+    ap.add_argument("--timesteps", type=int, default=200)
+    ap.add_argument("--radius", type=int, default=5, choices=[4, 5])
+    ap.add_argument("--graph", type=int, default=20, help="time steps per captured CUDA graph")
+    ap.add_argument("--tile", type=str, default="", help="tx,ty,zchunk of the tiled kernel")
+    ap.add_argument("--naive", action="store_true", help="time the one-thread-per-point kernel")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-timesteps", type=int, default=10)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("sweep_tiled.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1310_8232_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None, None
+    want = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[0] == kernel_tag and parts[1] == want:
+                return float(parts[2]), parts[3]
+    return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        fd, self.path = tempfile.mkstemp(suffix=".csv", prefix="clocks_")
+        os.close(fd)
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+            os.remove(self.path)
+        except OSError:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload_config(args, extra=None):
+    cfg = {"workload": f"single shot {args.n}^3 FP32, 8-layer random velocity model (seed 1310), "
+                       f"R={args.radius} ({2 * args.radius}th-order space / 2nd-order time), "
+                       f"{args.timesteps} time steps, dx=10 m, dt=0.5 CFL, 15 Hz Ricker at centre",
+           "nx": args.n, "ny": args.n, "nz": args.n, "radius": args.radius,
+           "timesteps": args.timesteps, "parallelism": "replicas (one independent shot per GPU)",
+           "l2": "no flush needed: every array (u, u_prev, kappa) is larger than L2"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def cpu_baseline(args, v, dt):
+    """The FP64 oracle, as it stands, on this host's cores: the first
+    --cpu-timesteps steps of the same shot."""
+    import numpy as np
+
+    import oracle
+    from paper_1310_8232_gb300 import workloads
+    steps = args.cpu_timesteps
+    t0 = time.perf_counter()
+    oracle.run(v.astype(np.float64), workloads.DX, dt, args.radius, steps)
+    el = time.perf_counter() - t0
+    pts = float(args.n) ** 3 * steps
+    return {"value": pts / el / 1e9, "unit": METRIC, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {steps} of {args.timesteps} time steps of the {args.n}^3 shot, "
+                      f"FP64 unblocked oracle, {el:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1310_8232_gb300 import workloads
+    v = workloads.layered_velocity(args.n, args.n, args.n, seed=1310).astype(np.float64)
+    dt = workloads.time_step(oracle.cfl_limit(args.radius), workloads.DX, float(v.max()))
+    per = max(1, min(args.cpu_timesteps, 2))
+    for _ in range(args.warmup):
+        oracle.run(v, workloads.DX, dt, args.radius, per)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(v, workloads.DX, dt, args.radius, per)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    pts = float(args.n) ** 3 * per * args.steps
+    val = pts / total / 1e9
+    sample = (f"each step: first {per} of {args.timesteps} time steps of the {args.n}^3 shot "
+              f"(FP64 unblocked oracle)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, {"sample_timesteps_per_step": per}),
+        "cpu_baseline": {"value": val, "unit": METRIC, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1310_8232_gb300 import binding as st
+    from paper_1310_8232_gb300 import workloads
+
+    n, R, T = args.n, args.radius, args.timesteps
+    v = workloads.layered_velocity(n, n, n, seed=1310)
+    dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(v.max()))
+    stream = torch.cuda.current_stream()
+    dv = torch.from_numpy(v).cuda()
+    if args.naive:
+        tile = (st.STENCIL_KERNEL_NAIVE, 0, 0, 0)
+    elif args.tile:
+        tx, ty, zc = (int(x) for x in args.tile.split(","))
+        tile = (st.STENCIL_KERNEL_TILED, tx, ty, zc)
+    else:
+        tile = None
+    desc = st.make_desc(dv, dt, radius=R, dx=workloads.DX, tile=tile, graph_steps=args.graph,
+                        stream=stream.cuda_stream)
+    t_plan = time.perf_counter()
+    plan = st.stencil_plan(desc)
+    plan_ms = 1e3 * (time.perf_counter() - t_plan)
+    stats = st.stencil_get_stats(plan)
+    t = stats.tile
+    kernel_tag = ("sweep_naive_kernel" if t.kernel == st.STENCIL_KERNEL_NAIVE
+                  else f"sweep_tiled_kernel<{R},{t.tx},{t.ty}>")
+
+    def shot():
+        st.stencil_set_fields(plan, None, None, 0)
+        st.stencil_step(plan, T)
+
+    for _ in range(args.warmup):
+        shot()
+    barrier()
+    # our kernels per shot: one sweep per time step, plus one step-counter
+    # kernel per captured graph and per eager chunk of <= 64 steps
+    if args.graph:
+        rem = T % args.graph
+        launches_per_shot = (T // args.graph) * (args.graph + 1) + rem + (rem + 63) // 64
+    else:
+        launches_per_shot = T + (T + 63) // 64
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for k in range(args.steps):
+            st.stencil_set_fields(plan, None, None, 0)
+            ev[k][0].record(stream)
+            st.stencil_step(plan, T)
+            ev[k][1].record(stream)
+        end.record(stream)
+        barrier()
+    st.stencil_sync(plan)
+    elapsed_ms = start.elapsed_time(end)
+    sweep_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    pts_per_shot = float(n) ** 3 * T
+    value = world * pts_per_shot * args.steps / (elapsed_ms / 1e3) / 1e9
+    kernel_ms = sweep_ms / (args.steps * T)
+    achieved = BYTES_PER_POINT * float(n) ** 3 / (kernel_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    if peaks and "hbm_gbs" in peaks:
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    else:
+        peak, peak_src = FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+    traffic, traffic_src = profiled_traffic(kernel_tag + f"@{n}")
+
+    e2e = None
+    if not args.no_e2e:
+        # Through the public API with host buffers: H2D of the velocity model
+        # (kappa recomputed on the device), one shot, D2H of the final field.
+        hv = torch.from_numpy(v).pin_memory()
+        hout = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+        for _ in range(1):
+            st.stencil_set_velocity(plan, hv)
+            st.stencil_set_fields(plan, None, None, 0)
+            st.stencil_run(plan, T, hout)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            st.stencil_set_velocity(plan, hv)
+            st.stencil_set_fields(plan, None, None, 0)
+            st.stencil_run(plan, T, hout)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * pts_per_shot * args.steps / e2e_s / 1e9, "unit": METRIC,
+               "h2d_bytes_per_step": int(hv.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
+               "api": "stencil_set_velocity(host pinned) + stencil_set_fields + stencil_run(out=host pinned)"}
+    st.stencil_destroy(plan)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args, v, dt)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, {
+                "tile": {"kernel": kernel_tag, "tx": t.tx, "ty": t.ty, "zchunk": t.zchunk},
+                "graph_steps": args.graph, "plan_ms": plan_ms}),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "kernel": kernel_tag,
+                         "bytes_per_point": BYTES_PER_POINT, "launch_ms": kernel_ms,
+                         "peak_source": peak_src, "traffic_source": traffic_src,
+                         "timing": "CUDA events around each shot's sweeps on the launching stream; "
+                                   "per-launch time = sum / launches (includes the step-counter kernel)"},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * launches_per_shot,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

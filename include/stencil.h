@@ -1,0 +1,226 @@
+/*
+ * libstencil -- GB300 (sm_103a) acoustic finite-difference stencil sweep.
+ *
+ * The operation (Sec. 2 of "Improving Memory Hierarchy Utilisation for
+ * Stencil Computations on Multicore Machines", Fig. 1a, and the time loop of
+ * Algorithm 1 "RTM()"): the "3D model" step of reverse-time migration, an
+ * explicit finite-difference solution of the acoustic wave equation, 2nd
+ * order in time and of order 2R in space (R = 5 is the paper's 10th order,
+ * "five points in each direction for each dimension"; R = 4 is 8th order).
+ * One time step n -> n+1 updates every grid point p:
+ *
+ *   u^{n+1}[p] = 2 u^n[p] - u^{n-1}[p] + kappa[p] * Lambda(u^n)[p]
+ *   kappa[p]   = v[p]^2 dt^2 / dx^2
+ *   Lambda(u)[p] = 3 c_0 u[p] + sum_{r=1..R} c_r (u[p -+ r e_x] + u[p -+ r e_y] + u[p -+ r e_z])
+ *   u^{n+1}[s] += src_amp * v[s]^2 dt^2 * w(n dt)      (point source at s)
+ *
+ * with c_r the exact central second-difference weights of order 2R,
+ * neighbours outside the grid read as 0 (homogeneous Dirichlet through ghost
+ * zeros), u^0 = u^{-1} = 0 by default, and w the Ricker wavelet
+ * w(t) = (1 - 2 pi^2 f^2 tau^2) exp(-pi^2 f^2 tau^2), tau = t - t0.
+ *
+ * Conventions for every entry point:
+ *   - returns STENCIL_OK (0) or a negative STENCIL_E* code; no C++ exception
+ *     crosses this boundary; stencil_last_error() gives a message for the
+ *     calling thread's last failure;
+ *   - arrays are 3D, x fastest, then y, then z: element (i,j,k) of a dense
+ *     array is at (k*ny + j)*nx + i; "dense" means exactly nx*ny*nz elements;
+ *   - the caller owns every array it passes; a plan copies what it keeps;
+ *   - a pointer flagged "on device" is a CUDA device pointer on the device
+ *     that was current when the plan was made; otherwise it is host memory;
+ *   - a plan is used by one host thread at a time; a shot server is
+ *     thread-safe.
+ */
+#ifndef STENCIL_H
+#define STENCIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STENCIL_API __attribute__((visibility("default")))
+#else
+#define STENCIL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define STENCIL_OK               0
+#define STENCIL_EINVAL          -1  /* bad argument: dims <= 0, radius not 4/5, null pointer, source outside grid, v <= 0 ... */
+#define STENCIL_ECFL            -2  /* dt above the stability bound for the largest velocity */
+#define STENCIL_ENOMEM          -3  /* device allocation failed */
+#define STENCIL_EBUDGET         -4  /* request larger than the whole memory budget */
+#define STENCIL_ETIMEOUT        -5  /* a bounded device-side wait gave up */
+#define STENCIL_ECUDA           -6  /* a CUDA call failed (message kept) */
+#define STENCIL_ENOTREADY       -7  /* result not available yet */
+#define STENCIL_EUNKNOWN_TICKET -8  /* no such shot ticket */
+#define STENCIL_ENODEV          -9  /* no usable CUDA device */
+#define STENCIL_EUNSUPPORTED   -10  /* configuration not built into this library */
+
+/* ---- enums ----------------------------------------------------------- */
+typedef enum {
+    STENCIL_FP32 = 0,   /* u, u_prev stored in FP32 */
+    STENCIL_FP16 = 1,   /* u, u_prev stored in FP16 with a per-z-plane FP32 scale */
+    STENCIL_BF16 = 2    /* u, u_prev stored in BF16 with a per-z-plane FP32 scale */
+} stencil_storage;
+
+typedef enum {
+    STENCIL_KERNEL_AUTO  = 0,  /* library default: the tiled kernel, default tile */
+    STENCIL_KERNEL_NAIVE = 1,  /* one thread per point, neighbours straight from global memory */
+    STENCIL_KERNEL_TILED = 2   /* 2.5D blocking: TMA-staged xy tile + halo, z-marching register queue */
+} stencil_kernel;
+
+/* Tile parameters of the tiled kernel, the GPU analogue of the paper's
+ * blocksize (i, j, k) (Sec. 3, Fig. 1b): tx x ty points of an xy plane per
+ * thread block, marching over zchunk planes in z.  tx in {32, 64, 128},
+ * ty in {4, 8, 16, 32}; zchunk >= 1 (0 = whole nz). */
+typedef struct {
+    int32_t kernel;     /* stencil_kernel */
+    int32_t tx, ty;
+    int32_t zchunk;
+} stencil_tile;
+
+/* How stencil_plan picks the tile (Sec. 3.2-3.3 re-run on GPU tile parameters). */
+typedef enum {
+    STENCIL_TUNE_NONE       = 0,  /* use desc.tile as given (kernel AUTO = default tile) */
+    STENCIL_TUNE_OWN        = 1,  /* library autotuner: time every feasible tile once, take the fastest */
+    STENCIL_TUNE_MWMB       = 2,  /* three-stage selection, stage 2 = max (Eq. 2) */
+    STENCIL_TUNE_OB         = 3,  /* original block: each stream its own candidates, global min */
+    STENCIL_TUNE_MMMB       = 4,  /* three-stage selection, stage 2 = min (Eq. 1) */
+    STENCIL_TUNE_MAMB       = 5,  /* three-stage selection, stage 2 = closest to mean (Eq. 3) */
+    STENCIL_TUNE_EXHAUSTIVE = 6   /* every feasible tile, timed with all streams running it */
+} stencil_tune_mode;
+
+/* Selection-phase parameters (Sec. 3.2): nI iterations per candidate, C
+ * concurrent streams (the "cores" that share L2 and HBM), N groups (the
+ * "nodes"), P parts per parameter axis for the candidate list (Sec. 3.7). */
+typedef struct {
+    int32_t parts;        /* P, default 5 */
+    int32_t iterations;   /* nI, default 8 */
+    int32_t streams;      /* C, default 4 */
+    int32_t groups;       /* N, default 2 */
+} stencil_tune_params;
+
+/* Problem description (the paper's statement of the problem: grid, order,
+ * spacing, time step, velocity model, source).  Initialise with
+ * stencil_desc_init() and then set fields. */
+typedef struct {
+    int32_t nx, ny, nz;          /* grid points per axis, >= 1 */
+    int32_t radius;              /* R = 4 (8th order) or 5 (10th order) */
+    double  dx;                  /* grid spacing, m (> 0) */
+    double  dt;                  /* time step, s (> 0, checked against the CFL bound) */
+    const float *velocity;       /* dense nx*ny*nz, m/s, every value > 0 and finite */
+    int32_t velocity_on_device;  /* 1 if velocity is a device pointer */
+    int32_t src_x, src_y, src_z; /* source grid index, inside the grid */
+    double  src_freq_hz;         /* Ricker peak frequency f (> 0) */
+    double  src_t0;              /* Ricker delay t0, s; < 0 means 1/f */
+    double  src_amp;             /* source amplitude multiplier; 0 = no source */
+    int32_t storage;             /* stencil_storage */
+    int32_t tune_mode;           /* stencil_tune_mode */
+    stencil_tile tile;           /* used when tune_mode == STENCIL_TUNE_NONE */
+    stencil_tune_params tune;    /* used by the selection modes */
+    void   *cuda_stream;         /* cudaStream_t to run on; NULL = the plan creates its own */
+    int32_t graph_steps;         /* steps per captured CUDA graph; 0 = launch step by step */
+} stencil_desc;
+
+/* Plan state, results of tuning and the device layout. */
+typedef struct {
+    int64_t steps_done;          /* n of the current level u^n */
+    stencil_tile tile;           /* tile in use */
+    double  vmax;                /* largest velocity */
+    double  cfl;                 /* vmax * dt / dx */
+    double  cfl_limit;           /* stability bound on vmax * dt / dx */
+    int64_t pitch;               /* row pitch of the device fields, elements */
+    int64_t field_bytes;         /* bytes of one device field */
+    int64_t device_bytes;        /* bytes the plan holds on the device */
+    /* tile selection (NaN when no selection ran) */
+    double  min_time_ms;         /* MinTime: best time of the selection phase (nI steps) */
+    double  actual_time_ms;      /* ActualTime: verification, chosen tile on the full grid (nI steps) */
+    double  quality;             /* (ActualTime - MinTime) / MinTime */
+    double  selection_ms;        /* wall time spent selecting */
+    int32_t n_candidates;        /* candidates timed */
+    int32_t tune_mode;
+} stencil_stats;
+
+typedef struct stencil_plan_s *stencil_plan_t;
+
+/* ---- plan lifecycle --------------------------------------------------- */
+
+/* Fill *d with defaults: radius 5, dx 10, src_freq 15 Hz, t0 = 1/f,
+ * src_amp 1, FP32 storage, no tuning, default tile, no graphs.  Dims,
+ * dt, velocity and source must still be set. */
+STENCIL_API void stencil_desc_init(stencil_desc *d);
+
+/* Build a plan on the current CUDA device: validate *d, allocate the two
+ * wavefield buffers and kappa on the device, compute kappa = v^2 dt^2/dx^2
+ * and vmax there, check vmax*dt/dx against the CFL bound (STENCIL_ECFL),
+ * zero u^0 and u^{-1}, and pick the tile (tune_mode).  Synchronous.  The
+ * velocity array is only read during this call. */
+STENCIL_API int stencil_plan(const stencil_desc *d, stencil_plan_t *out);
+
+/* Release every device resource of the plan (synchronises its stream). */
+STENCIL_API int stencil_destroy(stencil_plan_t p);
+
+/* ---- stepping --------------------------------------------------------- */
+
+/* Enqueue nsteps time steps (Algorithm 1's loop, the 3D-model step, with the
+ * source) on the plan's stream; returns without waiting.  nsteps >= 0. */
+STENCIL_API int stencil_step(stencil_plan_t p, int32_t nsteps);
+
+/* stencil_step(nsteps), then copy u^n (dense, nx*ny*nz floats) to out_u
+ * (host or device per out_on_device; NULL = no copy), then wait for the
+ * stream and report any device-side error. */
+STENCIL_API int stencil_run(stencil_plan_t p, int32_t nsteps, float *out_u, int32_t out_on_device);
+
+/* Wait for the plan's stream; report device-side errors (STENCIL_ETIMEOUT). */
+STENCIL_API int stencil_sync(stencil_plan_t p);
+
+/* ---- state ------------------------------------------------------------ */
+
+/* Copy u^n (which = 0) or u^{n-1} (which = 1) out as a dense FP32 array.
+ * Synchronous. */
+STENCIL_API int stencil_get_field(stencil_plan_t p, int32_t which, float *out, int32_t out_on_device);
+
+/* Set the state: u^n = u, u^{n-1} = u_prev (dense FP32; NULL = zeros), and
+ * the step counter n = step.  Synchronous. */
+STENCIL_API int stencil_set_fields(stencil_plan_t p, const float *u, const float *u_prev,
+                       int32_t on_device, int64_t step);
+
+/* Replace the velocity model of an existing plan (dense nx*ny*nz, host or
+ * device): recompute kappa and vmax on the device and re-check the CFL bound
+ * with the plan's dt (STENCIL_ECFL leaves the plan unusable until a valid
+ * model is set).  The wavefields and step counter are left as they are.
+ * Enqueued on the plan's stream; waits for it before returning. */
+STENCIL_API int stencil_set_velocity(stencil_plan_t p, const float *velocity, int32_t on_device);
+
+STENCIL_API int stencil_get_stats(stencil_plan_t p, stencil_stats *s);
+
+/* ---- FP64 validation reductions (on the device, deterministic) -------- */
+
+/* Discrete energy between the two current levels,
+ *   E = sum_p (u^n - u^{n-1})^2 / kappa - u^n * Lambda(u^{n-1}),
+ * evaluated in FP64; conserved by the scheme without a source. */
+STENCIL_API int stencil_energy(stencil_plan_t p, double *out);
+
+/* ||u^n - ref|| / ||ref|| in FP64; ref is a dense FP64 device array. */
+STENCIL_API int stencil_rel_l2(stencil_plan_t p, const double *ref_device, double *out);
+
+/* ---- helpers ---------------------------------------------------------- */
+
+/* Stability bound on v*dt/dx of the 3D leapfrog scheme of radius R:
+ * 2 / sqrt(3 W), W = |c_0| + 2 sum |c_r|.  Returns < 0 for an unsupported R. */
+STENCIL_API double stencil_cfl_limit(int32_t radius);
+
+/* Message for the calling thread's last failed call ("" if none). */
+STENCIL_API const char *stencil_last_error(void);
+
+/* Library version string. */
+STENCIL_API const char *stencil_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STENCIL_H */

@@ -148,11 +148,29 @@ static inline double at(const grid_t *g, const double *u, long i, long j, long k
 
 /* Lambda(u) at one point, unit spacing.  Fixed order: centre term, then
  * r ascending, and within each r the six neighbours -x,+x,-y,+y,-z,+z summed
- * left to right before the multiply by c_r. */
+ * left to right before the multiply by c_r.  Points at least R away from
+ * every face read their neighbours directly; the others through at(); both
+ * paths evaluate the same expression in the same order. */
 static inline double lap_point(const grid_t *g, const double *u, long i, long j, long k)
 {
+    const int R = g->R;
+    if (i >= R && i < g->nx - R && j >= R && j < g->ny - R && k >= R && k < g->nz - R) {
+        const long sx = 1, sy = g->nx, sz = (long)g->nx * g->ny;
+        const double *c = u + (k * g->ny + j) * (long)g->nx + i;
+        double acc = 3.0 * g->c[0] * c[0];
+        for (int r = 1; r <= R; ++r) {
+            double s = c[-r * sx];
+            s += c[r * sx];
+            s += c[-r * sy];
+            s += c[r * sy];
+            s += c[-r * sz];
+            s += c[r * sz];
+            acc += g->c[r] * s;
+        }
+        return acc;
+    }
     double acc = 3.0 * g->c[0] * at(g, u, i, j, k);
-    for (int r = 1; r <= g->R; ++r) {
+    for (int r = 1; r <= R; ++r) {
         double s = at(g, u, i - r, j, k);
         s += at(g, u, i + r, j, k);
         s += at(g, u, i, j - r, k);
@@ -215,8 +233,10 @@ int oracle_run(const oracle_problem *p, int steps, int bi, int bj, int bk,
     if (bj <= 0 || bj > ny) bj = (int)ny;
     if (bk <= 0 || bk > nz) bk = (int)nz;
     double *kappa = (double *)malloc(sizeof(double) * n);
-    double *next = (double *)malloc(sizeof(double) * n);
-    if (!kappa || !next) { free(kappa); free(next); return -1; }
+    double *spare = (double *)malloc(sizeof(double) * n);
+    if (!kappa || !spare) { free(kappa); free(spare); return -1; }
+    double *const u_out = u, *const up_out = u_prev;
+    double *next = spare;
     const double dt2 = p->dt * p->dt, dx2 = p->dx * p->dx;
     for (long q = 0; q < n; ++q) kappa[q] = p->v[q] * p->v[q] * dt2 / dx2;
     const int has_src = p->amp != 0.0 && p->sx >= 0 && p->sx < nx && p->sy >= 0 &&
@@ -224,18 +244,24 @@ int oracle_run(const oracle_problem *p, int steps, int bi, int bj, int bk,
     const long s = has_src ? ((long)p->sz * ny + p->sy) * nx + p->sx : 0;
     const long nbk = (nz + bk - 1) / bk;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #else
     (void)nthreads;
+    const int nt = 1;
 #endif
     for (int step = 0; step < steps; ++step) {
-        #pragma omp parallel for schedule(static)
+        /* OpenMP splits the k-blocks when there are enough of them, else the
+         * planes inside each block; either way each point is written once
+         * with the same expression. */
+        const int par_blocks = nbk >= 2 * nt;
+        #pragma omp parallel for schedule(static) if (par_blocks) num_threads(nt)
         for (long kb = 0; kb < nbk; ++kb) {
             const long k0 = kb * bk, k1 = (k0 + bk < nz) ? k0 + bk : nz;
             for (long j0 = 0; j0 < ny; j0 += bj) {
                 const long j1 = (j0 + bj < ny) ? j0 + bj : ny;
                 for (long i0 = 0; i0 < nx; i0 += bi) {
                     const long i1 = (i0 + bi < nx) ? i0 + bi : nx;
+                    #pragma omp parallel for schedule(static) if (!par_blocks) num_threads(nt)
                     for (long k = k0; k < k1; ++k)
                         for (long j = j0; j < j1; ++j)
                             for (long i = i0; i < i1; ++i) {
@@ -249,12 +275,23 @@ int oracle_run(const oracle_problem *p, int steps, int bi, int bj, int bk,
             const double t = (double)(p->n0 + step) * p->dt;
             next[s] += p->amp * p->v[s] * p->v[s] * dt2 * oracle_ricker(p->f, p->t0, t);
         }
-        /* rotate: u_prev <- u, u <- next */
-        memcpy(u_prev, u, sizeof(double) * n);
-        memcpy(u, next, sizeof(double) * n);
+        /* rotate: u_prev <- u, u <- next (the old u_prev buffer is reused) */
+        double *old_prev = u_prev;
+        u_prev = u;
+        u = next;
+        next = old_prev;
+    }
+    /* Each step rotates (u, u_prev, next) -> (next, u, u_prev); move the
+     * results back into the caller's two arrays. */
+    if (u == spare) {              /* steps = 1 mod 3: u_prev is u_out */
+        memcpy(up_out, u_out, sizeof(double) * n);
+        memcpy(u_out, spare, sizeof(double) * n);
+    } else if (u == up_out) {      /* steps = 2 mod 3: u_prev is spare */
+        memcpy(u_out, up_out, sizeof(double) * n);
+        memcpy(up_out, spare, sizeof(double) * n);
     }
     free(kappa);
-    free(next);
+    free(spare);
     return 0;
 }
 

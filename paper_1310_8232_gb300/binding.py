@@ -1,0 +1,255 @@
+"""ctypes binding of libstencil (include/stencil.h): same names, argument marshalling only.
+
+Every step of the sweep runs in the CUDA library; this module only converts
+Python values to the C structures and pointers and turns negative status
+codes into ``StencilError``.  Importing it fails loudly if the library has not
+been built (``python -m paper_1310_8232_gb300.build``); there is no fallback.
+
+Arrays: numpy arrays are passed as host pointers; torch CUDA tensors are
+passed as device pointers (PyTorch provides device memory and streams only).
+All arrays are float32 (velocity, fields) or float64 (reference fields) of
+shape (nz, ny, nx), C-contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libstencil.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1310_8232_gb300.build` "
+                      "(or __graft_entry__.build()); the sweep has no non-CUDA fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- constants (mirror include/stencil.h) ----------------------------------
+STENCIL_OK = 0
+STENCIL_EINVAL = -1
+STENCIL_ECFL = -2
+STENCIL_ENOMEM = -3
+STENCIL_EBUDGET = -4
+STENCIL_ETIMEOUT = -5
+STENCIL_ECUDA = -6
+STENCIL_ENOTREADY = -7
+STENCIL_EUNKNOWN_TICKET = -8
+STENCIL_ENODEV = -9
+STENCIL_EUNSUPPORTED = -10
+
+STENCIL_FP32, STENCIL_FP16, STENCIL_BF16 = 0, 1, 2
+STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_TILED = 0, 1, 2
+(STENCIL_TUNE_NONE, STENCIL_TUNE_OWN, STENCIL_TUNE_MWMB, STENCIL_TUNE_OB, STENCIL_TUNE_MMMB,
+ STENCIL_TUNE_MAMB, STENCIL_TUNE_EXHAUSTIVE) = range(7)
+
+_CODE_NAMES = {v: k for k, v in globals().items() if k.startswith("STENCIL_E")}
+
+
+class StencilError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_CODE_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ---- structures --------------------------------------------------------------
+class stencil_tile(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("tx", ctypes.c_int32), ("ty", ctypes.c_int32),
+                ("zchunk", ctypes.c_int32)]
+
+
+class stencil_tune_params(ctypes.Structure):
+    _fields_ = [("parts", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("groups", ctypes.c_int32)]
+
+
+class stencil_desc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("radius", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("velocity", ctypes.c_void_p), ("velocity_on_device", ctypes.c_int32),
+        ("src_x", ctypes.c_int32), ("src_y", ctypes.c_int32), ("src_z", ctypes.c_int32),
+        ("src_freq_hz", ctypes.c_double), ("src_t0", ctypes.c_double), ("src_amp", ctypes.c_double),
+        ("storage", ctypes.c_int32), ("tune_mode", ctypes.c_int32),
+        ("tile", stencil_tile), ("tune", stencil_tune_params),
+        ("cuda_stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int32),
+    ]
+
+
+class stencil_stats(ctypes.Structure):
+    _fields_ = [
+        ("steps_done", ctypes.c_int64), ("tile", stencil_tile),
+        ("vmax", ctypes.c_double), ("cfl", ctypes.c_double), ("cfl_limit", ctypes.c_double),
+        ("pitch", ctypes.c_int64), ("field_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("min_time_ms", ctypes.c_double), ("actual_time_ms", ctypes.c_double),
+        ("quality", ctypes.c_double), ("selection_ms", ctypes.c_double),
+        ("n_candidates", ctypes.c_int32), ("tune_mode", ctypes.c_int32),
+    ]
+
+
+# ---- prototypes ----------------------------------------------------------------
+_P = ctypes.c_void_p
+_I = ctypes.c_int32
+_lib.stencil_desc_init.argtypes = [ctypes.POINTER(stencil_desc)]
+_lib.stencil_desc_init.restype = None
+_lib.stencil_plan.argtypes = [ctypes.POINTER(stencil_desc), ctypes.POINTER(_P)]
+_lib.stencil_destroy.argtypes = [_P]
+_lib.stencil_step.argtypes = [_P, _I]
+_lib.stencil_run.argtypes = [_P, _I, _P, _I]
+_lib.stencil_sync.argtypes = [_P]
+_lib.stencil_get_field.argtypes = [_P, _I, _P, _I]
+_lib.stencil_set_fields.argtypes = [_P, _P, _P, _I, ctypes.c_int64]
+_lib.stencil_set_velocity.argtypes = [_P, _P, _I]
+_lib.stencil_get_stats.argtypes = [_P, ctypes.POINTER(stencil_stats)]
+_lib.stencil_energy.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
+_lib.stencil_rel_l2.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_double)]
+_lib.stencil_cfl_limit.argtypes = [_I]
+_lib.stencil_cfl_limit.restype = ctypes.c_double
+_lib.stencil_last_error.restype = ctypes.c_char_p
+_lib.stencil_version.restype = ctypes.c_char_p
+for _name in ("stencil_plan", "stencil_destroy", "stencil_step", "stencil_run", "stencil_sync",
+              "stencil_get_field", "stencil_set_fields", "stencil_get_stats", "stencil_energy",
+              "stencil_rel_l2", "stencil_set_velocity"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise StencilError(rc, (_lib.stencil_last_error() or b"").decode())
+    return rc
+
+
+def _ptr(a) -> tuple[int, int]:
+    """(address, on_device) of a numpy array or a torch tensor; None -> (0, 0)."""
+    if a is None:
+        return 0, 0
+    if hasattr(a, "data_ptr"):          # torch.Tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return int(a.data_ptr()), int(a.is_cuda)
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return int(a.ctypes.data), 0
+
+
+# ---- C-ABI calls, same names --------------------------------------------------
+def stencil_desc_init() -> stencil_desc:
+    d = stencil_desc()
+    _lib.stencil_desc_init(ctypes.byref(d))
+    return d
+
+
+def stencil_plan(desc: stencil_desc, velocity=None) -> int:
+    """Create a plan; ``velocity`` (numpy float32 or CUDA tensor) overrides desc.velocity.
+    Returns the opaque plan handle (an int)."""
+    if velocity is not None:
+        addr, dev = _ptr(velocity)
+        desc.velocity = addr
+        desc.velocity_on_device = dev
+    h = _P()
+    _check(_lib.stencil_plan(ctypes.byref(desc), ctypes.byref(h)))
+    return h.value
+
+
+def stencil_destroy(plan: int) -> None:
+    _check(_lib.stencil_destroy(plan))
+
+
+def stencil_step(plan: int, nsteps: int) -> None:
+    _check(_lib.stencil_step(plan, nsteps))
+
+
+def stencil_run(plan: int, nsteps: int, out=None) -> None:
+    addr, dev = _ptr(out)
+    _check(_lib.stencil_run(plan, nsteps, addr or None, dev))
+
+
+def stencil_sync(plan: int) -> None:
+    _check(_lib.stencil_sync(plan))
+
+
+def stencil_get_field(plan: int, which: int, out) -> None:
+    addr, dev = _ptr(out)
+    _check(_lib.stencil_get_field(plan, which, addr, dev))
+
+
+def stencil_set_fields(plan: int, u=None, u_prev=None, step: int = 0) -> None:
+    au, du = _ptr(u)
+    ap, dp = _ptr(u_prev)
+    if u is not None and u_prev is not None and du != dp:
+        raise ValueError("u and u_prev must both be host or both be device arrays")
+    _check(_lib.stencil_set_fields(plan, au or None, ap or None, du or dp, step))
+
+
+def stencil_set_velocity(plan: int, velocity) -> None:
+    addr, dev = _ptr(velocity)
+    _check(_lib.stencil_set_velocity(plan, addr, dev))
+
+
+def stencil_get_stats(plan: int) -> stencil_stats:
+    s = stencil_stats()
+    _check(_lib.stencil_get_stats(plan, ctypes.byref(s)))
+    return s
+
+
+def stencil_energy(plan: int) -> float:
+    v = ctypes.c_double()
+    _check(_lib.stencil_energy(plan, ctypes.byref(v)))
+    return v.value
+
+
+def stencil_rel_l2(plan: int, ref_device) -> float:
+    addr, dev = _ptr(ref_device)
+    if not dev:
+        raise ValueError("reference must be a CUDA float64 tensor")
+    v = ctypes.c_double()
+    _check(_lib.stencil_rel_l2(plan, addr, ctypes.byref(v)))
+    return v.value
+
+
+def stencil_cfl_limit(radius: int) -> float:
+    return float(_lib.stencil_cfl_limit(radius))
+
+
+def stencil_last_error() -> str:
+    return (_lib.stencil_last_error() or b"").decode()
+
+
+def stencil_version() -> str:
+    return (_lib.stencil_version() or b"").decode()
+
+
+# ---- convenience -----------------------------------------------------------------
+def make_desc(velocity, dt: float, radius: int = 5, dx: float = 10.0, src=None, f: float = 15.0,
+              t0: float = -1.0, amp: float = 1.0, tile=None, graph_steps: int = 0, stream=None,
+              tune_mode: int = STENCIL_TUNE_NONE, storage: int = STENCIL_FP32) -> stencil_desc:
+    """Descriptor for a velocity array of shape (nz, ny, nx); src defaults to the centre."""
+    nz, ny, nx = (int(s) for s in velocity.shape)
+    d = stencil_desc_init()
+    d.nx, d.ny, d.nz = nx, ny, nz
+    d.radius = radius
+    d.dx, d.dt = float(dx), float(dt)
+    sx, sy, sz = src if src is not None else (nx // 2, ny // 2, nz // 2)
+    d.src_x, d.src_y, d.src_z = int(sx), int(sy), int(sz)
+    d.src_freq_hz, d.src_t0, d.src_amp = float(f), float(t0), float(amp)
+    d.storage = storage
+    d.tune_mode = tune_mode
+    if tile is not None:
+        kernel, tx, ty, zc = tile
+        d.tile = stencil_tile(kernel, tx, ty, zc)
+    d.graph_steps = graph_steps
+    if stream is not None:
+        d.cuda_stream = int(stream)
+    addr, dev = _ptr(velocity)
+    d.velocity = addr
+    d.velocity_on_device = dev
+    return d
+
+
+EXPORTED = [
+    "stencil_desc_init", "stencil_plan", "stencil_destroy", "stencil_step", "stencil_run",
+    "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
+    "stencil_get_stats",
+    "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
+    "stencil_version",
+]

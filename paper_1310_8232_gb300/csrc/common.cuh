@@ -1,0 +1,178 @@
+// Shared device-side definitions of libstencil: finite-difference weights,
+// the wavelet, launch parameter blocks and the mbarrier / TMA wrappers.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace stencil {
+
+// Device-side error bits, OR-ed into the plan's error word.
+enum : int { ERR_TIMEOUT = 1, ERR_BAD_STATE = 2 };
+
+// Exact central 2nd-difference weights of order 2R (Sec. 2, "10th order in
+// space": R = 5; R = 4 also built), c_0..c_R as rationals num/den.  These
+// make the symmetric stencil exact on polynomials of degree <= 2R+1; the
+// paper prints no coefficients.
+template <int R>
+__host__ __device__ constexpr double wnum(int r);
+template <int R>
+__host__ __device__ constexpr double wden(int r);
+template <>
+__host__ __device__ constexpr double wnum<4>(int r)
+{
+    return r == 0 ? -205.0 : r == 1 ? 8.0 : r == 2 ? -1.0 : r == 3 ? 8.0 : -1.0;
+}
+template <>
+__host__ __device__ constexpr double wden<4>(int r)
+{
+    return r == 0 ? 72.0 : r == 1 ? 5.0 : r == 2 ? 5.0 : r == 3 ? 315.0 : 560.0;
+}
+template <>
+__host__ __device__ constexpr double wnum<5>(int r)
+{
+    return r == 0 ? -5269.0 : r == 1 ? 5.0 : r == 2 ? -5.0 : r == 3 ? 5.0 : r == 4 ? -5.0 : 1.0;
+}
+template <>
+__host__ __device__ constexpr double wden<5>(int r)
+{
+    return r == 0 ? 1800.0 : r == 1 ? 3.0 : r == 2 ? 21.0 : r == 3 ? 126.0 : r == 4 ? 1008.0 : 3150.0;
+}
+template <int R>
+__host__ __device__ constexpr float wf(int r) { return (float)(wnum<R>(r) / wden<R>(r)); }
+template <int R>
+__host__ __device__ constexpr double wd(int r) { return wnum<R>(r) / wden<R>(r); }
+
+// Ricker wavelet of peak frequency f centred on t0, in FP64.
+__device__ __forceinline__ double ricker(double f, double t0, double t)
+{
+    const double pi = 3.141592653589793238462643;
+    const double a = pi * pi * f * f * (t - t0) * (t - t0);
+    return (1.0 - 2.0 * a) * exp(-a);
+}
+
+// Point source: u^{n+1}[s] += scale * w(n dt), scale = amp * v_s^2 dt^2.
+struct Source {
+    int32_t on;          // 0 = no source
+    int32_t x, y, z;
+    double scale;
+    double f, t0, dt;
+};
+
+// Per-launch parameters of one sweep (one time step) over one grid.
+struct SweepParams {
+    int32_t nx, ny, nz;
+    int64_t pitch;                 // row pitch, elements
+    int64_t plane;                 // pitch * ny
+    const float *u;                // u^n
+    float *up;                     // in: u^{n-1}; out: u^{n+1} (in place)
+    const float *kappa;            // v^2 dt^2 / dx^2
+    int32_t zchunk;                // planes per thread block in z
+    int32_t tiles_x;               // tiles along x (tiled kernel)
+    Source src;
+    const int64_t *step_base;      // device: n of the first step of this launch chunk
+    int32_t step_off;              // this launch's offset within the chunk
+    int *err;                      // device error word
+};
+
+__device__ __forceinline__ int64_t current_step(const SweepParams &p)
+{
+    return *p.step_base + p.step_off;
+}
+
+// ---- PTX wrappers (mbarrier + TMA; sm_90 and later, used on sm_103a) ----
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `bar` with the given parity, giving up after
+// `limit_ns` nanoseconds: then set ERR_TIMEOUT in *err and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          uint64_t limit_ns = 2000000000ull)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 3D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y,
+                                            int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// Same, with an L2 cache-policy hint (createpolicy result).
+__device__ __forceinline__ void tma_load_3d_hint(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                                 int y, int z, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+}  // namespace stencil

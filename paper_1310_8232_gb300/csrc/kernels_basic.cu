@@ -1,0 +1,234 @@
+// K0 (naive sweep), K4 (coefficient init + velocity range), K5 (FP64
+// validation reductions) and the step-counter kernel.
+#include <math.h>
+
+#include "internal.h"
+
+namespace stencil {
+
+// ---------------------------------------------------------------------------
+// K0: one thread per grid point; every neighbour is read from global memory
+// with an explicit bounds test (ghost zeros).  The GPU counterpart of the
+// paper's "No-Blocksize" variant (Sec. 3.1): no data staging at all.
+// grid (ceil(nx/128), ny, nz), 128 threads.
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx) return;
+    const int64_t q = (int64_t)z * p.plane + (int64_t)y * p.pitch + x;
+    const float *u = p.u;
+    const float c = u[q];
+    float acc = 3.0f * wf<R>(0) * c;
+#pragma unroll
+    for (int r = 1; r <= R; ++r) {
+        float s = (x - r >= 0) ? u[q - r] : 0.0f;
+        s += (x + r < p.nx) ? u[q + r] : 0.0f;
+        s += (y - r >= 0) ? u[q - r * p.pitch] : 0.0f;
+        s += (y + r < p.ny) ? u[q + r * p.pitch] : 0.0f;
+        s += (z - r >= 0) ? u[q - r * p.plane] : 0.0f;
+        s += (z + r < p.nz) ? u[q + r * p.plane] : 0.0f;
+        acc = fmaf(wf<R>(r), s, acc);
+    }
+    float nxt = fmaf(p.kappa[q], acc, 2.0f * c - p.up[q]);
+    if (p.src.on && x == p.src.x && y == p.src.y && z == p.src.z) {
+        const double t = (double)current_step(p) * p.src.dt;
+        nxt += (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
+    }
+    p.up[q] = nxt;
+}
+
+cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)
+{
+    if (p.ny > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
+    dim3 grid((p.nx + 127) / 128, p.ny, p.nz);
+    if (R == 4)
+        sweep_naive_kernel<4><<<grid, 128, 0, s>>>(p);
+    else if (R == 5)
+        sweep_naive_kernel<5><<<grid, 128, 0, s>>>(p);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K4: kappa[p] = v[p]^2 dt^2 / dx^2 (FP64 product, rounded once to FP32),
+// written over the pitched copy of v; also the largest velocity (bit pattern
+// max, valid for positive floats) and the number of invalid velocities.
+// ---------------------------------------------------------------------------
+__global__ void coef_init_kernel(float *kv, int nx, int ny, int nz, int64_t pitch, double dt2_dx2,
+                                 unsigned *vmax_bits, unsigned long long *n_bad)
+{
+    unsigned local_max = 0;
+    unsigned local_bad = 0;
+    const int64_t rows = (int64_t)ny * nz;
+    const int64_t total = rows * nx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / nx;
+        const int x = (int)(i - row * nx);
+        const int64_t q = row * pitch + x;
+        const float v = kv[q];
+        if (!(v > 0.0f) || !isfinite(v)) {
+            ++local_bad;
+            kv[q] = 0.0f;
+        } else {
+            local_max = max(local_max, __float_as_uint(v));
+            const double vd = (double)v;
+            kv[q] = (float)(vd * vd * dt2_dx2);
+        }
+    }
+    local_max = __reduce_max_sync(0xffffffffu, local_max);
+    local_bad = __reduce_add_sync(0xffffffffu, local_bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (local_max) atomicMax(vmax_bits, local_max);
+        if (local_bad) atomicAdd(n_bad, (unsigned long long)local_bad);
+    }
+}
+
+cudaError_t launch_coef_init(float *kv, int nx, int ny, int nz, int64_t pitch, double dt2_dx2,
+                             unsigned *vmax_bits, unsigned long long *n_bad, cudaStream_t s)
+{
+    coef_init_kernel<<<1216, 256, 0, s>>>(kv, nx, ny, nz, pitch, dt2_dx2, vmax_bits, n_bad);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K5: FP64 reductions.  Each thread walks a fixed grid-stride sequence, each
+// block reduces in a fixed tree, one block sums the per-block partials in
+// index order: the result depends only on the data, not on scheduling.
+// ---------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ void block_sum_store(double (&v)[N], double *dst)
+{
+    __shared__ double red[N][RED_THREADS / 32];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) s += red[k][w];
+            dst[k] = s;
+        }
+    }
+}
+
+template <int N>
+__global__ void sum_partials_kernel(const double *partials, int nblocks, double *out)
+{
+    // one block: thread t sums partials t, t+256, ... in order, then the tree
+    double v[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < N; ++k) v[k] += partials[(int64_t)b * N + k];
+    block_sum_store<N>(v, out);
+}
+
+template <int R>
+__device__ __forceinline__ double at_d(const float *u, int x, int y, int z, int nx, int ny, int nz,
+                                       int64_t pitch, int64_t plane)
+{
+    if (x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz) return 0.0;
+    return (double)u[(int64_t)z * plane + (int64_t)y * pitch + x];
+}
+
+template <int R>
+__global__ void __launch_bounds__(RED_THREADS) energy_kernel(const float *u1, const float *u0,
+                                                             const float *kappa, int nx, int ny, int nz,
+                                                             int64_t pitch, double *partials)
+{
+    const int64_t plane = pitch * ny;
+    const int64_t total = (int64_t)nx * ny * nz;
+    double e[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / nx;
+        const int x = (int)(i - row * nx);
+        const int z = (int)(row / ny);
+        const int y = (int)(row - (int64_t)z * ny);
+        const int64_t q = (int64_t)z * plane + (int64_t)y * pitch + x;
+        double lap = 3.0 * wd<R>(0) * (double)u0[q];
+#pragma unroll
+        for (int r = 1; r <= R; ++r) {
+            double s = at_d<R>(u0, x - r, y, z, nx, ny, nz, pitch, plane);
+            s += at_d<R>(u0, x + r, y, z, nx, ny, nz, pitch, plane);
+            s += at_d<R>(u0, x, y - r, z, nx, ny, nz, pitch, plane);
+            s += at_d<R>(u0, x, y + r, z, nx, ny, nz, pitch, plane);
+            s += at_d<R>(u0, x, y, z - r, nx, ny, nz, pitch, plane);
+            s += at_d<R>(u0, x, y, z + r, nx, ny, nz, pitch, plane);
+            lap += wd<R>(r) * s;
+        }
+        const double a = (double)u1[q];
+        const double d = a - (double)u0[q];
+        e[0] += d * d / (double)kappa[q] - a * lap;
+    }
+    block_sum_store<1>(e, partials + blockIdx.x);
+}
+
+cudaError_t launch_energy(int R, const float *u1, const float *u0, const float *kappa, int nx, int ny, int nz,
+                          int64_t pitch, double *partials, double *out, cudaStream_t s)
+{
+    if (R == 4)
+        energy_kernel<4><<<RED_BLOCKS, RED_THREADS, 0, s>>>(u1, u0, kappa, nx, ny, nz, pitch, partials);
+    else if (R == 5)
+        energy_kernel<5><<<RED_BLOCKS, RED_THREADS, 0, s>>>(u1, u0, kappa, nx, ny, nz, pitch, partials);
+    else
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<1><<<1, RED_THREADS, 0, s>>>(partials, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(RED_THREADS) sqdiff_kernel(const float *a, const double *b, int nx, int ny,
+                                                             int nz, int64_t pitch, double *partials)
+{
+    const int64_t plane = pitch * ny;
+    const int64_t total = (int64_t)nx * ny * nz;
+    double v[2] = {0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / nx;
+        const int x = (int)(i - row * nx);
+        const int z = (int)(row / ny);
+        const int y = (int)(row - (int64_t)z * ny);
+        const double av = (double)a[(int64_t)z * plane + (int64_t)y * pitch + x];
+        const double bv = b[i];
+        const double d = av - bv;
+        v[0] += d * d;
+        v[1] += bv * bv;
+    }
+    block_sum_store<2>(v, partials + 2 * blockIdx.x);
+}
+
+cudaError_t launch_sqdiff(const float *a, const double *b, int nx, int ny, int nz, int64_t pitch,
+                          double *partials, double *out, cudaStream_t s)
+{
+    sqdiff_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, nx, ny, nz, pitch, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_partials_kernel<2><<<1, RED_THREADS, 0, s>>>(partials, RED_BLOCKS, out);
+    return cudaGetLastError();
+}
+
+__global__ void advance_kernel(int64_t *n, int k) { *n += k; }
+
+cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s)
+{
+    advance_kernel<<<1, 1, 0, s>>>(n, k);
+    return cudaGetLastError();
+}
+
+}  // namespace stencil

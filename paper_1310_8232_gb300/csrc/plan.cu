@@ -1,0 +1,624 @@
+// Host runtime behind the C-ABI of include/stencil.h: plan lifecycle, step
+// enqueueing (eager or through captured CUDA graphs), state transfer, FP64
+// validation reductions.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "plan_impl.h"
+#include "stencil.h"
+
+namespace stencil {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int fail_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(STENCIL_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(STENCIL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+double cfl_limit(int R)
+{
+    double W;
+    if (R == 4) {
+        W = std::fabs(wd<4>(0));
+        for (int r = 1; r <= 4; ++r) W += 2.0 * std::fabs(wd<4>(r));
+    } else if (R == 5) {
+        W = std::fabs(wd<5>(0));
+        for (int r = 1; r <= 5; ++r) W += 2.0 * std::fabs(wd<5>(r));
+    } else {
+        return -1.0;
+    }
+    return 2.0 / std::sqrt(3.0 * W);
+}
+
+int64_t row_pitch(int nx)
+{
+    return ((int64_t)nx + 31) / 32 * 32;   // 128-byte rows for FP32
+}
+
+// ---- TMA descriptors --------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw,
+               int bh)
+{
+    auto fn = encode_fn();
+    if (!fn) return fail(STENCIL_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
+    const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * esize), (cuuint64_t)(pitch * ny * esize)};
+    cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(STENCIL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return STENCIL_OK;
+}
+
+// ---- plan internals -----------------------------------------------------------
+int Plan::build_maps()
+{
+    if (tile.kernel != STENCIL_KERNEL_TILED) return STENCIL_OK;
+    int smem, threads, hx;
+    if (!tiled_config(R, tile.tx, tile.ty, &smem, &threads, &hx))
+        return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not built for radius %d", tile.tx, tile.ty, R);
+    for (int b = 0; b < 2; ++b) {
+        int rc = encode_map(&maps_halo[b], buf[b], nx, ny, nz, pitch, 4, tile.tx + 2 * hx, tile.ty + 2 * R);
+        if (rc) return rc;
+        rc = encode_map(&maps_core[b], buf[b], nx, ny, nz, pitch, 4, tile.tx, tile.ty);
+        if (rc) return rc;
+    }
+    return encode_map(&map_kcore, kappa, nx, ny, nz, pitch, 4, tile.tx, tile.ty);
+}
+
+SweepParams Plan::params(int parity, int step_off) const
+{
+    SweepParams s{};
+    s.nx = nx;
+    s.ny = ny;
+    s.nz = nz;
+    s.pitch = pitch;
+    s.plane = pitch * ny;
+    s.u = buf[parity];
+    s.up = buf[parity ^ 1];
+    s.kappa = kappa;
+    s.zchunk = tile.zchunk > 0 ? tile.zchunk : nz;
+    s.tiles_x = 0;
+    s.src = src;
+    s.step_base = d_step;
+    s.step_off = step_off;
+    s.err = d_err;
+    return s;
+}
+
+cudaError_t Plan::launch_one(int parity, int step_off, cudaStream_t s) const
+{
+    const SweepParams prm = params(parity, step_off);
+    if (tile.kernel == STENCIL_KERNEL_NAIVE) return launch_naive(R, prm, s);
+    TiledMaps m;
+    m.u_halo = maps_halo[parity];
+    m.up_core = maps_core[parity ^ 1];
+    m.k_core = map_kcore;
+    return launch_tiled(R, tile.tx, tile.ty, m, prm, s);
+}
+
+int Plan::enqueue_eager(int nsteps)
+{
+    int done = 0;
+    while (done < nsteps) {
+        const int k = std::min(nsteps - done, 64);
+        for (int i = 0; i < k; ++i) {
+            cudaError_t e = launch_one(cur, i, stream);
+            if (e != cudaSuccess) return fail_cuda(e, "sweep launch");
+            cur ^= 1;
+        }
+        cudaError_t e = launch_advance(d_step, k, stream);
+        if (e != cudaSuccess) return fail_cuda(e, "step counter");
+        done += k;
+    }
+    return STENCIL_OK;
+}
+
+int Plan::capture_graphs()
+{
+    drop_graphs();
+    for (int par = 0; par < 2; ++par) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamBeginCapture");
+        int c = par;
+        cudaError_t le = cudaSuccess;
+        for (int i = 0; i < graph_len && le == cudaSuccess; ++i) {
+            le = launch_one(c, i, stream);
+            c ^= 1;
+        }
+        if (le == cudaSuccess) le = launch_advance(d_step, graph_len, stream);
+        e = cudaStreamEndCapture(stream, &g);
+        if (le != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail_cuda(le, "launch during graph capture");
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&graph_exec[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+    }
+    return STENCIL_OK;
+}
+
+void Plan::drop_graphs()
+{
+    for (auto &g : graph_exec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+int Plan::enqueue(int nsteps)
+{
+    if (nsteps < 0) return fail(STENCIL_EINVAL, "nsteps < 0");
+    if (!velocity_ok) return fail(STENCIL_EINVAL, "the plan has no valid velocity model");
+    int left = nsteps;
+    if (graph_len > 0 && left >= graph_len) {
+        if (!graph_exec[0]) {
+            int rc = capture_graphs();
+            if (rc) return rc;
+        }
+        while (left >= graph_len) {
+            cudaError_t e = cudaGraphLaunch(graph_exec[cur], stream);
+            if (e != cudaSuccess) return fail_cuda(e, "cudaGraphLaunch");
+            left -= graph_len;   // graph_len is even: parity unchanged
+        }
+    }
+    int rc = enqueue_eager(left);
+    if (rc) return rc;
+    steps_done += nsteps;
+    return STENCIL_OK;
+}
+
+int Plan::check_device_error()
+{
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return fail_cuda(e, "stream synchronize");
+    if (h) {
+        cudaMemsetAsync(d_err, 0, sizeof(int), stream);
+        cudaStreamSynchronize(stream);
+        if (h & ERR_TIMEOUT) return fail(STENCIL_ETIMEOUT, "a device-side wait timed out");
+        return fail(STENCIL_ECUDA, "device error word 0x%x", h);
+    }
+    return STENCIL_OK;
+}
+
+void Plan::release()
+{
+    if (stream) cudaStreamSynchronize(stream);
+    drop_graphs();
+    for (auto &b : buf)
+        if (b) cudaFree(b);
+    if (kappa) cudaFree(kappa);
+    if (d_scratch) cudaFree(d_scratch);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    buf[0] = buf[1] = nullptr;
+    kappa = nullptr;
+    d_scratch = nullptr;
+    stream = nullptr;
+}
+
+// v (dense, host or device) -> pitched kappa buffer, then kappa = v^2 dt^2 /
+// dx^2 in place (K4), vmax and the count of invalid values read back; checks
+// the CFL bound.  Synchronous on the plan's stream.
+int Plan::load_velocity(const float *v, int on_device)
+{
+    cudaStream_t s = stream;
+    cudaError_t e = cudaMemcpy2DAsync(kappa, pitch * sizeof(float), v, (size_t)nx * sizeof(float),
+                                      (size_t)nx * sizeof(float), (size_t)ny * nz,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail_cuda(e, "velocity copy");
+    if ((e = cudaMemsetAsync(d_vmax, 0, sizeof(unsigned), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_bad, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+        return fail_cuda(e, "cudaMemsetAsync");
+    e = launch_coef_init(kappa, nx, ny, nz, pitch, (dt * dt) / (dx * dx), d_vmax, d_bad, s);
+    if (e != cudaSuccess) return fail_cuda(e, "coef_init");
+    unsigned vmax_bits = 0;
+    unsigned long long nbad = 0;
+    cudaMemcpyAsync(&vmax_bits, d_vmax, sizeof vmax_bits, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&nbad, d_bad, sizeof nbad, cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail_cuda(e, "velocity setup");
+    velocity_ok = false;
+    if (nbad) return fail(STENCIL_EINVAL, "%llu velocities are not finite and > 0", nbad);
+    float vm;
+    std::memcpy(&vm, &vmax_bits, sizeof vm);
+    vmax = vm;
+    cfl_lim = cfl_limit(R);
+    cfl = (double)vm * dt / dx;
+    if (cfl > cfl_lim * (1.0 + 1e-12))
+        return fail(STENCIL_ECFL, "vmax*dt/dx = %.6g exceeds the stability bound %.6g", cfl, cfl_lim);
+    velocity_ok = true;
+    return STENCIL_OK;
+}
+
+int default_zchunk(int nz)
+{
+    return std::min(nz, 64);
+}
+
+stencil_tile default_tile(int nz)
+{
+    stencil_tile t;
+    t.kernel = STENCIL_KERNEL_TILED;
+    t.tx = 64;
+    t.ty = 16;
+    t.zchunk = default_zchunk(nz);
+    return t;
+}
+
+int validate_desc(const stencil_desc *d)
+{
+    if (!d) return fail(STENCIL_EINVAL, "null descriptor");
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0) return fail(STENCIL_EINVAL, "grid dims must be >= 1");
+    if (d->ny > 65535 || d->nz > 65535 || d->nx > (1 << 24))
+        return fail(STENCIL_EINVAL, "grid dims too large");
+    if (d->radius != 4 && d->radius != 5) return fail(STENCIL_EINVAL, "radius must be 4 or 5");
+    if (!(d->dx > 0) || !std::isfinite(d->dx)) return fail(STENCIL_EINVAL, "dx must be > 0");
+    if (!(d->dt > 0) || !std::isfinite(d->dt)) return fail(STENCIL_EINVAL, "dt must be > 0");
+    if (!d->velocity) return fail(STENCIL_EINVAL, "null velocity");
+    if (d->src_amp != 0.0) {
+        if (d->src_x < 0 || d->src_x >= d->nx || d->src_y < 0 || d->src_y >= d->ny || d->src_z < 0 ||
+            d->src_z >= d->nz)
+            return fail(STENCIL_EINVAL, "source outside the grid");
+        if (!(d->src_freq_hz > 0)) return fail(STENCIL_EINVAL, "source frequency must be > 0");
+    }
+    if (d->storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "storage %d not built", d->storage);
+    if (d->graph_steps < 0 || (d->graph_steps & 1))
+        return fail(STENCIL_EINVAL, "graph_steps must be 0 or a positive even number");
+    if (d->tune_mode < STENCIL_TUNE_NONE || d->tune_mode > STENCIL_TUNE_EXHAUSTIVE)
+        return fail(STENCIL_EINVAL, "bad tune_mode");
+    return STENCIL_OK;
+}
+
+int check_tile(int R, const stencil_tile &t)
+{
+    if (t.kernel == STENCIL_KERNEL_NAIVE) return STENCIL_OK;
+    if (t.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EINVAL, "bad kernel id %d", t.kernel);
+    if (t.zchunk < 0) return fail(STENCIL_EINVAL, "zchunk must be >= 0");
+    int smem, threads, hx;
+    if (!tiled_config(R, t.tx, t.ty, &smem, &threads, &hx))
+        return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not available for radius %d", t.tx, t.ty, R);
+    return STENCIL_OK;
+}
+
+int plan_create(const stencil_desc *d, Plan **out)
+{
+    int rc = validate_desc(d);
+    if (rc) return rc;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STENCIL_ENODEV, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    Plan *p = new Plan();
+    p->dev = dev;
+    p->R = d->radius;
+    p->nx = d->nx;
+    p->ny = d->ny;
+    p->nz = d->nz;
+    p->dx = d->dx;
+    p->dt = d->dt;
+    p->pitch = row_pitch(d->nx);
+    p->field_elems = p->pitch * d->ny * d->nz;
+    p->graph_len = d->graph_steps;
+    p->tune_mode = d->tune_mode;
+    auto bail = [&](int code) {
+        p->release();
+        delete p;
+        return code;
+    };
+    if (d->cuda_stream) {
+        p->stream = static_cast<cudaStream_t>(d->cuda_stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "cudaStreamCreate"));
+        p->own_stream = true;
+    }
+    const size_t fbytes = (size_t)p->field_elems * sizeof(float);
+    for (auto &b : p->buf) {
+        e = cudaMalloc(&b, fbytes);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(field)"));
+    }
+    e = cudaMalloc(&p->kappa, fbytes);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(kappa)"));
+    // scratch: step counter, error word, v range, reduction partials and result
+    const size_t scratch = 256 + sizeof(double) * (2 * RED_BLOCKS + 8);
+    e = cudaMalloc(&p->d_scratch, scratch);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(scratch)"));
+    unsigned char *sc = static_cast<unsigned char *>(p->d_scratch);
+    p->d_step = reinterpret_cast<int64_t *>(sc);
+    p->d_err = reinterpret_cast<int *>(sc + 8);
+    p->d_vmax = reinterpret_cast<unsigned *>(sc + 16);
+    p->d_bad = reinterpret_cast<unsigned long long *>(sc + 24);
+    p->d_result = reinterpret_cast<double *>(sc + 64);
+    p->d_partials = reinterpret_cast<double *>(sc + 256);
+    p->device_bytes = 3 * (int64_t)fbytes + (int64_t)scratch;
+
+    cudaStream_t s = p->stream;
+    if ((e = cudaMemsetAsync(p->d_scratch, 0, scratch, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->buf[0], 0, fbytes, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->buf[1], 0, fbytes, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->kappa, 0, fbytes, s)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMemsetAsync"));
+    float v_src = 0.0f;
+    if (d->src_amp != 0.0) {
+        const float *vs = d->velocity + ((int64_t)d->src_z * d->ny + d->src_y) * d->nx + d->src_x;
+        e = cudaMemcpyAsync(&v_src, vs, sizeof(float),
+                            d->velocity_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "source velocity read"));
+    }
+    p->src_amp = d->src_amp;
+    rc = p->load_velocity(d->velocity, d->velocity_on_device);
+    if (rc) return bail(rc);
+
+    p->src.on = d->src_amp != 0.0;
+    p->src.x = d->src_x;
+    p->src.y = d->src_y;
+    p->src.z = d->src_z;
+    p->src.f = d->src_freq_hz;
+    p->src.t0 = d->src_t0 < 0 ? 1.0 / d->src_freq_hz : d->src_t0;
+    p->src.dt = d->dt;
+    p->src.scale = d->src_amp * (double)v_src * (double)v_src * d->dt * d->dt;
+
+    // tile
+    stencil_tile t = d->tile;
+    if (t.kernel == STENCIL_KERNEL_AUTO) t = default_tile(d->nz);
+    if (t.zchunk == 0) t.zchunk = d->nz;
+    rc = check_tile(p->R, t);
+    if (rc) return bail(rc);
+    p->tile = t;
+    rc = p->build_maps();
+    if (rc) return bail(rc);
+    if (d->tune_mode != STENCIL_TUNE_NONE) {
+        rc = tune_plan(p, d);
+        if (rc) return bail(rc);
+    }
+    *out = p;
+    return STENCIL_OK;
+}
+
+}  // namespace stencil
+
+using namespace stencil;
+
+extern "C" {
+
+void stencil_desc_init(stencil_desc *d)
+{
+    if (!d) return;
+    std::memset(d, 0, sizeof *d);
+    d->radius = 5;
+    d->dx = 10.0;
+    d->src_freq_hz = 15.0;
+    d->src_t0 = -1.0;
+    d->src_amp = 1.0;
+    d->storage = STENCIL_FP32;
+    d->tune_mode = STENCIL_TUNE_NONE;
+    d->tile.kernel = STENCIL_KERNEL_AUTO;
+    d->tune.parts = 5;
+    d->tune.iterations = 8;
+    d->tune.streams = 4;
+    d->tune.groups = 2;
+}
+
+int stencil_plan(const stencil_desc *d, stencil_plan_t *out)
+{
+    if (!out) return fail(STENCIL_EINVAL, "null output handle");
+    *out = nullptr;
+    Plan *p = nullptr;
+    int rc = plan_create(d, &p);
+    if (rc) return rc;
+    *out = reinterpret_cast<stencil_plan_t>(p);
+    return STENCIL_OK;
+}
+
+int stencil_destroy(stencil_plan_t h)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null plan");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    p->release();
+    delete p;
+    return STENCIL_OK;
+}
+
+int stencil_step(stencil_plan_t h, int32_t nsteps)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null plan");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    return p->enqueue(nsteps);
+}
+
+static int copy_out(Plan *p, const float *src, float *out, int on_device)
+{
+    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)p->nx * sizeof(float), src, p->pitch * sizeof(float),
+                                      (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "field copy out");
+    return STENCIL_OK;
+}
+
+int stencil_run(stencil_plan_t h, int32_t nsteps, float *out_u, int32_t out_on_device)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null plan");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    int rc = p->enqueue(nsteps);
+    if (rc) return rc;
+    if (out_u) {
+        rc = copy_out(p, p->buf[p->cur], out_u, out_on_device);
+        if (rc) return rc;
+    }
+    return p->check_device_error();
+}
+
+int stencil_sync(stencil_plan_t h)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null plan");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    return p->check_device_error();
+}
+
+int stencil_get_field(stencil_plan_t h, int32_t which, float *out, int32_t out_on_device)
+{
+    if (!h || !out) return fail(STENCIL_EINVAL, "null argument");
+    if (which != 0 && which != 1) return fail(STENCIL_EINVAL, "which must be 0 or 1");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    int rc = copy_out(p, p->buf[p->cur ^ which], out, out_on_device);
+    if (rc) return rc;
+    return p->check_device_error();
+}
+
+int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, int32_t on_device, int64_t step)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null plan");
+    if (step < 0) return fail(STENCIL_EINVAL, "step must be >= 0");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    const float *src[2] = {u, u_prev};
+    for (int k = 0; k < 2; ++k) {
+        float *dst = p->buf[p->cur ^ k];
+        cudaError_t e;
+        if (src[k])
+            e = cudaMemcpy2DAsync(dst, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
+                                  (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream);
+        else
+            e = cudaMemsetAsync(dst, 0, (size_t)p->field_elems * sizeof(float), p->stream);
+        if (e != cudaSuccess) return fail_cuda(e, "field copy in");
+    }
+    cudaError_t e = cudaMemcpyAsync(p->d_step, &step, sizeof step, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "step counter copy");
+    p->steps_done = step;
+    return p->check_device_error();
+}
+
+int stencil_set_velocity(stencil_plan_t h, const float *velocity, int32_t on_device)
+{
+    if (!h || !velocity) return fail(STENCIL_EINVAL, "null argument");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    float v_src = 0.0f;
+    if (p->src.on) {
+        const float *vs = velocity + ((int64_t)p->src.z * p->ny + p->src.y) * p->nx + p->src.x;
+        cudaError_t e = cudaMemcpyAsync(&v_src, vs, sizeof(float),
+                                        on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, p->stream);
+        if (e != cudaSuccess) return fail_cuda(e, "source velocity read");
+    }
+    int rc = p->load_velocity(velocity, on_device);
+    if (rc) return rc;
+    p->src.scale = p->src_amp * (double)v_src * (double)v_src * p->dt * p->dt;
+    p->drop_graphs();   // captured launches carry the old source scale
+    return STENCIL_OK;
+}
+
+int stencil_get_stats(stencil_plan_t h, stencil_stats *s)
+{
+    if (!h || !s) return fail(STENCIL_EINVAL, "null argument");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    std::memset(s, 0, sizeof *s);
+    s->steps_done = p->steps_done;
+    s->tile = p->tile;
+    s->vmax = p->vmax;
+    s->cfl = p->cfl;
+    s->cfl_limit = p->cfl_lim;
+    s->pitch = p->pitch;
+    s->field_bytes = p->field_elems * (int64_t)sizeof(float);
+    s->device_bytes = p->device_bytes;
+    s->min_time_ms = p->min_time_ms;
+    s->actual_time_ms = p->actual_time_ms;
+    s->quality = p->quality;
+    s->selection_ms = p->selection_ms;
+    s->n_candidates = p->n_candidates;
+    s->tune_mode = p->tune_mode;
+    return STENCIL_OK;
+}
+
+int stencil_energy(stencil_plan_t h, double *out)
+{
+    if (!h || !out) return fail(STENCIL_EINVAL, "null argument");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    cudaError_t e = launch_energy(p->R, p->buf[p->cur], p->buf[p->cur ^ 1], p->kappa, p->nx, p->ny, p->nz, p->pitch,
+                                  p->d_partials, p->d_result, p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "energy");
+    e = cudaMemcpyAsync(out, p->d_result, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "energy copy");
+    return p->check_device_error();
+}
+
+int stencil_rel_l2(stencil_plan_t h, const double *ref, double *out)
+{
+    if (!h || !ref || !out) return fail(STENCIL_EINVAL, "null argument");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    cudaError_t e = launch_sqdiff(p->buf[p->cur], ref, p->nx, p->ny, p->nz, p->pitch, p->d_partials, p->d_result,
+                                  p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "rel_l2");
+    double h2[2];
+    e = cudaMemcpyAsync(h2, p->d_result, sizeof h2, cudaMemcpyDeviceToHost, p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "rel_l2 copy");
+    int rc = p->check_device_error();
+    if (rc) return rc;
+    *out = h2[1] > 0 ? std::sqrt(h2[0] / h2[1]) : (h2[0] == 0 ? 0.0 : INFINITY);
+    return STENCIL_OK;
+}
+
+double stencil_cfl_limit(int32_t radius) { return cfl_limit(radius); }
+
+const char *stencil_last_error(void) { return g_last_error.c_str(); }
+
+const char *stencil_version(void) { return "libstencil 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// The plan object behind stencil_plan_t, shared by the runtime translation units.
+#pragma once
+
+#include <cmath>
+#include <string>
+
+#include "internal.h"
+#include "stencil.h"
+
+namespace stencil {
+
+int fail(int code, const char *fmt, ...);
+int fail_cuda(cudaError_t e, const char *what);
+double cfl_limit(int R);
+int64_t row_pitch(int nx);
+int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw, int bh);
+int check_tile(int R, const stencil_tile &t);
+stencil_tile default_tile(int nz);
+extern thread_local std::string g_last_error;
+
+struct Plan {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int R = 5;
+    int nx = 0, ny = 0, nz = 0;
+    double dx = 0, dt = 0;
+    int64_t pitch = 0;
+    int64_t field_elems = 0;
+    float *buf[2] = {nullptr, nullptr};   // buf[cur] = u^n, buf[cur ^ 1] = u^{n-1}
+    float *kappa = nullptr;
+    int cur = 0;
+    void *d_scratch = nullptr;
+    int64_t *d_step = nullptr;
+    int *d_err = nullptr;
+    unsigned *d_vmax = nullptr;
+    unsigned long long *d_bad = nullptr;
+    double *d_partials = nullptr;
+    double *d_result = nullptr;
+    int64_t device_bytes = 0;
+    int64_t steps_done = 0;
+    double vmax = 0, cfl = 0, cfl_lim = 0;
+    bool velocity_ok = false;
+    double src_amp = 0;
+    Source src{};
+    stencil_tile tile{};
+    CUtensorMap maps_halo[2];
+    CUtensorMap maps_core[2];
+    CUtensorMap map_kcore;
+    int graph_len = 0;
+    cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    // tile selection results
+    int tune_mode = 0;
+    double min_time_ms = NAN, actual_time_ms = NAN, quality = NAN, selection_ms = NAN;
+    int n_candidates = 0;
+
+    int build_maps();
+    int load_velocity(const float *v, int on_device);
+    SweepParams params(int parity, int step_off) const;
+    cudaError_t launch_one(int parity, int step_off, cudaStream_t s) const;
+    int enqueue_eager(int nsteps);
+    int enqueue(int nsteps);
+    int capture_graphs();
+    void drop_graphs();
+    int check_device_error();
+    void release();
+};
+
+// Tile selection (Sec. 3.2-3.3 on GPU tile parameters); sets p->tile.
+int tune_plan(Plan *p, const stencil_desc *d);
+
+}  // namespace stencil

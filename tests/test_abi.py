@@ -1,0 +1,97 @@
+"""The C-ABI library loads and exports every declared symbol; host-side
+validation and helpers behave (CPU only, no compute calls)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+import oracle
+
+
+def declared_symbols():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        names += re.findall(r"STENCIL_API\s+[\w\s\*]*?\b((?:stencil|shot)_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def st():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_1310_8232_gb300 import binding
+    return binding
+
+
+def test_library_exports_every_declared_symbol(st):
+    lib = ctypes.CDLL(st.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(st):
+    for n in declared_symbols():
+        assert hasattr(st, n), n
+
+
+def test_version(st):
+    assert "sm_103a" in st.stencil_version()
+
+
+@pytest.mark.parametrize("R", [4, 5])
+def test_cfl_limit_agrees_with_oracle(st, R):
+    # Independent implementations (library weights table vs oracle closed form).
+    assert st.stencil_cfl_limit(R) == pytest.approx(oracle.cfl_limit(R), rel=1e-14)
+
+
+def test_cfl_limit_rejects_unsupported_radius(st):
+    assert st.stencil_cfl_limit(3) < 0
+
+
+def test_desc_init_defaults(st):
+    d = st.stencil_desc_init()
+    assert d.radius == 5 and d.dx == 10.0 and d.src_freq_hz == 15.0
+    assert d.src_t0 < 0 and d.src_amp == 1.0
+    assert d.storage == st.STENCIL_FP32 and d.tune_mode == st.STENCIL_TUNE_NONE
+    assert d.tune.parts == 5 and d.graph_steps == 0
+
+
+def _desc(st, **kw):
+    v = np.full((8, 8, 8), 2000.0, dtype=np.float32)
+    d = st.make_desc(v, dt=1e-3, radius=4)
+    for k, val in kw.items():
+        setattr(d, k, val)
+    return d, v
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 0), ("ny", -1), ("radius", 3), ("radius", 6), ("dx", 0.0), ("dt", -1.0),
+    ("src_x", 8), ("src_z", -1), ("graph_steps", 3), ("tune_mode", 9),
+])
+def test_invalid_descriptors_rejected_before_device(st, field, value):
+    d, v = _desc(st, **{field: value})
+    with pytest.raises(st.StencilError) as ei:
+        st.stencil_plan(d)
+    assert ei.value.code == st.STENCIL_EINVAL
+
+
+def test_null_velocity_rejected(st):
+    d, v = _desc(st)
+    d.velocity = None
+    with pytest.raises(st.StencilError) as ei:
+        st.stencil_plan(d)
+    assert ei.value.code == st.STENCIL_EINVAL
+
+
+def test_null_handles_rejected(st):
+    for fn, args in ((st._lib.stencil_step, (None, 1)), (st._lib.stencil_sync, (None,)),
+                     (st._lib.stencil_destroy, (None,))):
+        assert fn(*args) == st.STENCIL_EINVAL
