@@ -242,7 +242,10 @@ def main():
     n, R, T = args.n, args.radius, args.timesteps
     v = workloads.layered_velocity(n, n, n, seed=1310)
     dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(v.max()))
-    stream = torch.cuda.current_stream()
+    # a dedicated stream, current for torch too: the plan's kernels, torch's
+    # copies and the timing events are all ordered on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     dv = torch.from_numpy(v).cuda()
     if args.naive:
         tile = (st.STENCIL_KERNEL_NAIVE, 0, 0, 0)

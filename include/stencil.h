@@ -122,7 +122,9 @@ typedef struct {
     int32_t tune_mode;           /* stencil_tune_mode */
     stencil_tile tile;           /* used when tune_mode == STENCIL_TUNE_NONE */
     stencil_tune_params tune;    /* used by the selection modes */
-    void   *cuda_stream;         /* cudaStream_t to run on; NULL = the plan creates its own */
+    void   *cuda_stream;         /* cudaStream_t to run on; NULL = the plan creates its own
+                                    non-blocking stream (the legacy default stream, handle 0,
+                                    cannot be requested: graphs cannot be captured on it) */
     int32_t graph_steps;         /* steps per captured CUDA graph; 0 = launch step by step */
 } stencil_desc;
 
@@ -137,8 +139,11 @@ typedef struct {
     int64_t field_bytes;         /* bytes of one device field */
     int64_t device_bytes;        /* bytes the plan holds on the device */
     /* tile selection (NaN when no selection ran) */
-    double  min_time_ms;         /* MinTime: best time of the selection phase (nI steps) */
-    double  actual_time_ms;      /* ActualTime: verification, chosen tile on the full grid (nI steps) */
+    double  min_time_ms;         /* MinTime: the chosen tile's selection-phase time (nI steps) */
+    double  actual_time_ms;      /* ActualTime: verification in the selection's setting (nI steps):
+                                    all C streams run the chosen tile together, max over streams
+                                    (full grid for OWN / EXHAUSTIVE) */
+    double  full_time_ms;        /* the chosen tile on the whole grid, nI steps */
     double  quality;             /* (ActualTime - MinTime) / MinTime */
     double  selection_ms;        /* wall time spent selecting */
     int32_t n_candidates;        /* candidates timed */
@@ -207,6 +212,30 @@ STENCIL_API int stencil_energy(stencil_plan_t p, double *out);
 
 /* ||u^n - ref|| / ||ref|| in FP64; ref is a dense FP64 device array. */
 STENCIL_API int stencil_rel_l2(stencil_plan_t p, const double *ref_device, double *out);
+
+/* ---- blocksize-selection building blocks (host only, no device work) ---- */
+
+/* Candidate values of one block axis of extent S split into P parts
+ * (Sec. 3.7): b = <1, S/(P-1)+1, 2S/(P-1)+1, ..., S>, integer division, the
+ * last value clamped to S, duplicates dropped.  Writes *n values to out
+ * (capacity cap; STENCIL_EINVAL if too small, *n still set). */
+STENCIL_API int stencil_candidates_1d(int32_t S, int32_t P, int32_t *out, int32_t cap, int32_t *n);
+
+/* Three-stage contention-aware selection (Sec. 3.3): times[(g*C + c)*K + k]
+ * is the time of group g's k-th candidate measured on stream c (all streams
+ * of a group run the same candidates in the same order; +inf marks a
+ * missing entry).  Stage 1: each stream's fastest candidate; stage 2: one
+ * stream per group by target 0 = min (MMMB, Eq. 1), 1 = max (MWMB, Eq. 2),
+ * 2 = closest to the group mean (MAMB, Eq. 3); stage 3: the group whose
+ * stage-2 time is smallest.  Ties go to the lowest index. */
+STENCIL_API int stencil_select(const double *times, int32_t groups, int32_t streams, int32_t cands,
+                               int32_t target, int32_t *group, int32_t *stream, int32_t *cand,
+                               double *time);
+
+/* Original Block (Sec. 3.3): times[c*K + k] is stream c's k-th own
+ * candidate; the global minimum wins. */
+STENCIL_API int stencil_select_ob(const double *times, int32_t streams, int32_t cands, int32_t *stream,
+                                  int32_t *cand, double *time);
 
 /* ---- helpers ---------------------------------------------------------- */
 

@@ -82,6 +82,7 @@ class stencil_stats(ctypes.Structure):
         ("vmax", ctypes.c_double), ("cfl", ctypes.c_double), ("cfl_limit", ctypes.c_double),
         ("pitch", ctypes.c_int64), ("field_bytes", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
         ("min_time_ms", ctypes.c_double), ("actual_time_ms", ctypes.c_double),
+        ("full_time_ms", ctypes.c_double),
         ("quality", ctypes.c_double), ("selection_ms", ctypes.c_double),
         ("n_candidates", ctypes.c_int32), ("tune_mode", ctypes.c_int32),
     ]
@@ -103,13 +104,19 @@ _lib.stencil_set_velocity.argtypes = [_P, _P, _I]
 _lib.stencil_get_stats.argtypes = [_P, ctypes.POINTER(stencil_stats)]
 _lib.stencil_energy.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_rel_l2.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_double)]
+_lib.stencil_candidates_1d.argtypes = [_I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]
+_lib.stencil_select.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I, ctypes.POINTER(_I),
+                                ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
+_lib.stencil_select_ob.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, ctypes.POINTER(_I),
+                                   ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_cfl_limit.argtypes = [_I]
 _lib.stencil_cfl_limit.restype = ctypes.c_double
 _lib.stencil_last_error.restype = ctypes.c_char_p
 _lib.stencil_version.restype = ctypes.c_char_p
 for _name in ("stencil_plan", "stencil_destroy", "stencil_step", "stencil_run", "stencil_sync",
               "stencil_get_field", "stencil_set_fields", "stencil_get_stats", "stencil_energy",
-              "stencil_rel_l2", "stencil_set_velocity"):
+              "stencil_rel_l2", "stencil_set_velocity", "stencil_candidates_1d", "stencil_select",
+              "stencil_select_ob"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -207,6 +214,40 @@ def stencil_rel_l2(plan: int, ref_device) -> float:
     return v.value
 
 
+def stencil_candidates_1d(S: int, P: int) -> list[int]:
+    out = (_I * max(P, 1))()
+    n = _I()
+    _check(_lib.stencil_candidates_1d(S, P, out, max(P, 1), ctypes.byref(n)))
+    return list(out[: n.value])
+
+
+def _times_array(times):
+    import numpy as np
+    a = np.ascontiguousarray(times, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def stencil_select(times, target: int) -> tuple[int, int, int, float]:
+    """times: array [groups][streams][cands]; returns (group, stream, cand, time)."""
+    a, p = _times_array(times)
+    g, s, c = _I(), _I(), _I()
+    t = ctypes.c_double()
+    G, C, K = a.shape
+    _check(_lib.stencil_select(p, G, C, K, target, ctypes.byref(g), ctypes.byref(s), ctypes.byref(c),
+                               ctypes.byref(t)))
+    return g.value, s.value, c.value, t.value
+
+
+def stencil_select_ob(times) -> tuple[int, int, float]:
+    """times: array [streams][cands]; returns (stream, cand, time)."""
+    a, p = _times_array(times)
+    s, c = _I(), _I()
+    t = ctypes.c_double()
+    C, K = a.shape
+    _check(_lib.stencil_select_ob(p, C, K, ctypes.byref(s), ctypes.byref(c), ctypes.byref(t)))
+    return s.value, c.value, t.value
+
+
 def stencil_cfl_limit(radius: int) -> float:
     return float(_lib.stencil_cfl_limit(radius))
 
@@ -251,5 +292,6 @@ EXPORTED = [
     "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
     "stencil_get_stats",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
+    "stencil_candidates_1d", "stencil_select", "stencil_select_ob",
     "stencil_version",
 ]

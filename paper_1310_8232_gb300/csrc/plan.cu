@@ -578,6 +578,7 @@ int stencil_get_stats(stencil_plan_t h, stencil_stats *s)
     s->device_bytes = p->device_bytes;
     s->min_time_ms = p->min_time_ms;
     s->actual_time_ms = p->actual_time_ms;
+    s->full_time_ms = p->full_time_ms;
     s->quality = p->quality;
     s->selection_ms = p->selection_ms;
     s->n_candidates = p->n_candidates;

@@ -51,7 +51,7 @@ struct Plan {
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     // tile selection results
     int tune_mode = 0;
-    double min_time_ms = NAN, actual_time_ms = NAN, quality = NAN, selection_ms = NAN;
+    double min_time_ms = NAN, actual_time_ms = NAN, full_time_ms = NAN, quality = NAN, selection_ms = NAN;
     int n_candidates = 0;
 
     int build_maps();

@@ -95,3 +95,56 @@ def test_null_handles_rejected(st):
     for fn, args in ((st._lib.stencil_step, (None, 1)), (st._lib.stencil_sync, (None,)),
                      (st._lib.stencil_destroy, (None,))):
         assert fn(*args) == st.STENCIL_EINVAL
+
+
+# ---- blocksize-selection building blocks vs the selection oracle ----------
+from oracle import selection  # noqa: E402
+
+
+@pytest.mark.parametrize("S,P", [(200, 5), (800, 5), (250, 10), (1500, 20), (3, 5), (1, 2), (7, 7),
+                                 (512, 5), (13, 4)])
+def test_candidates_1d_matches_oracle(st, S, P):
+    assert st.stencil_candidates_1d(S, P) == selection.candidates_1d(S, P)
+
+
+def test_candidates_1d_paper_example(st):
+    from conftest import read_golden
+    for row in read_golden("paper_candidates.txt"):
+        assert st.stencil_candidates_1d(int(row[0]), int(row[1])) == [int(x) for x in row[2:]]
+
+
+@pytest.mark.parametrize("seed", range(20))
+@pytest.mark.parametrize("target,name", [(0, "min"), (1, "max"), (2, "avg")])
+def test_three_stage_matches_oracle(st, seed, target, name):
+    rng = np.random.default_rng(seed)
+    G, C, K = rng.integers(1, 4), rng.integers(1, 6), rng.integers(1, 7)
+    # coarse values so that ties happen
+    t = rng.integers(1, 6, size=(G, C, K)).astype(np.float64)
+    g, s, c, tt = st.stencil_select(t, target)
+    og, oc, ot = selection.three_stage(t.tolist(), name)
+    assert (g, c, tt) == (og, oc, ot)
+    # the chosen stream's stage-1 pick is that candidate
+    assert t[g, s, c] == tt
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_original_block_matches_oracle(st, seed):
+    rng = np.random.default_rng(100 + seed)
+    C, K = rng.integers(1, 6), rng.integers(1, 7)
+    t = rng.integers(1, 9, size=(C, K)).astype(np.float64)
+    assert st.stencil_select_ob(t) == selection.original_block(t.tolist())
+
+
+def test_three_stage_skips_missing_entries(st):
+    t = np.full((2, 2, 3), np.inf)
+    t[0, :, :2] = [[3.0, 2.0], [4.0, 5.0]]
+    t[1, :, :1] = [[6.0], [1.0]]
+    g, s, c, tt = st.stencil_select(t, 1)       # MWMB: node0 max(2,4)=4; node1 max(6,1)=6
+    assert (g, s, c, tt) == (0, 1, 0, 4.0)
+
+
+def test_selection_rejects_bad_arguments(st):
+    with pytest.raises(st.StencilError):
+        st.stencil_select(np.ones((1, 1, 1)), 3)
+    with pytest.raises(st.StencilError):
+        st.stencil_candidates_1d(0, 5)

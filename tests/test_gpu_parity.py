@@ -25,6 +25,9 @@ def env():
     __graft_entry__.build()
     from paper_1310_8232_gb300 import binding as st
     torch.cuda.set_device(0)
+    # one non-default stream, current for torch and used by every plan, so
+    # that torch's copies and the plans' kernels are ordered
+    torch.cuda.set_stream(torch.cuda.Stream())
     return torch, st
 
 
@@ -33,8 +36,7 @@ def run_gpu(env, v, dt, R, steps, tile=None, src=None, amp=1.0, u0=None, um1=Non
     torch, st = env
     vel = torch.from_numpy(v).cuda() if on_device else v
     d = st.make_desc(vel, dt, radius=R, dx=workloads.DX, src=src, amp=amp, tile=tile,
-                     graph_steps=graph_steps,
-                     stream=torch.cuda.current_stream().cuda_stream)
+                     graph_steps=graph_steps, stream=cur_stream(torch))
     plan = st.stencil_plan(d)
     try:
         if u0 is not None or um1 is not None or n0:
@@ -57,6 +59,10 @@ def check(got, ref, tol=TOL):
     worst = np.max(np.abs(got.astype(np.float64) - ref))
     assert worst <= tol * scale, f"max abs error {worst:.3e} vs scale {scale:.3e}"
     return err
+
+
+def cur_stream(torch):
+    return torch.cuda.current_stream().cuda_stream
 
 
 NAIVE = (1, 0, 0, 0)
@@ -168,7 +174,7 @@ def test_split_runs_equal_one_run(env):
     n, R = 40, 4
     v = workloads.layered_velocity(n, n, n, seed=14)
     dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
-    d = st.make_desc(v, dt, radius=R)
+    d = st.make_desc(v, dt, radius=R, stream=cur_stream(torch))
     plan = st.stencil_plan(d)
     try:
         st.stencil_step(plan, 13)
@@ -228,7 +234,7 @@ def test_device_rel_l2_matches_host(env):
     n, R = 33, 4
     v = workloads.layered_velocity(n, n, n, seed=17)
     dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
-    d = st.make_desc(v, dt, radius=R)
+    d = st.make_desc(v, dt, radius=R, stream=cur_stream(torch))
     plan = st.stencil_plan(d)
     try:
         out = np.empty_like(v)
@@ -327,8 +333,7 @@ def test_full_size_512_cube_sampled_points(env, R):
     u0 = workloads.random_field(n, n, n, seed=31)
     um1 = workloads.random_field(n, n, n, seed=32)
     src = (n // 2, n // 2, n // 2)
-    d = st.make_desc(torch.from_numpy(v).cuda(), dt, radius=R, graph_steps=2,
-                     stream=torch.cuda.current_stream().cuda_stream)
+    d = st.make_desc(torch.from_numpy(v).cuda(), dt, radius=R, graph_steps=2, stream=cur_stream(torch))
     plan = st.stencil_plan(d)
     try:
         st.stencil_set_fields(plan, torch.from_numpy(u0).cuda(), torch.from_numpy(um1).cuda(), step=60)
