@@ -237,6 +237,34 @@ STENCIL_API int stencil_select(const double *times, int32_t groups, int32_t stre
 STENCIL_API int stencil_select_ob(const double *times, int32_t streams, int32_t cands, int32_t *stream,
                                   int32_t *cand, double *time);
 
+/* ---- FP64 sums of squares without device allocation -------------------- */
+
+/* The paper has no counterpart to this entry point; it is a library service
+ * for callers that cannot call cudaMalloc: for example a process whose
+ * device memory is all held by a caching allocator (PyTorch's keeps freed
+ * memory for itself), or a latency-critical loop that must not stall on
+ * cudaMalloc / cudaFree (cudaFree synchronises the device).
+ *
+ * Computes out[0] = sum (a - b)^2 and out[1] = sum b^2 over the nx*ny*nz
+ * points in FP64 (||a - b|| / ||b|| = sqrt(out[0] / out[1])):
+ *   a       FP32 device array, ny*nz rows of nx values, row pitch a_pitch
+ *           elements (a_pitch >= nx; a dense array has a_pitch = nx);
+ *   b       dense FP64 device array of nx*ny*nz values;
+ *   out     2 doubles of device memory, written by the call;
+ *   stream  cudaStream_t to enqueue on (NULL = the legacy default stream);
+ *           the call returns without waiting.
+ * Allocates nothing: the per-block partial sums live in a 256 KiB array in
+ * the library's static device memory, which every GPU that loads the
+ * library holds until the process exits.  Limit: nx*ny*nz <= 2^28
+ * (268435456) elements, else STENCIL_EINVAL before any device work.  All
+ * calls share that array and it keeps the last call's contents (each call
+ * overwrites the slots it reads, so nothing needs clearing); calls that
+ * overlap on the GPU, e.g. on two streams, race on it.  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture. */
+STENCIL_API int stencil_sqdiff_noalloc(const float *a, int64_t a_pitch, const double *b, int32_t nx,
+                                       int32_t ny, int32_t nz, double *out, void *stream);
+
 /* ---- helpers ---------------------------------------------------------- */
 
 /* Stability bound on v*dt/dx of the 3D leapfrog scheme of radius R:

@@ -109,6 +109,7 @@ _lib.stencil_select.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
                                 ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_select_ob.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, ctypes.POINTER(_I),
                                    ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
+_lib.stencil_sqdiff_noalloc.argtypes = [_P, ctypes.c_int64, _P, _I, _I, _I, _P, _P]
 _lib.stencil_cfl_limit.argtypes = [_I]
 _lib.stencil_cfl_limit.restype = ctypes.c_double
 _lib.stencil_last_error.restype = ctypes.c_char_p
@@ -116,7 +117,7 @@ _lib.stencil_version.restype = ctypes.c_char_p
 for _name in ("stencil_plan", "stencil_destroy", "stencil_step", "stencil_run", "stencil_sync",
               "stencil_get_field", "stencil_set_fields", "stencil_get_stats", "stencil_energy",
               "stencil_rel_l2", "stencil_set_velocity", "stencil_candidates_1d", "stencil_select",
-              "stencil_select_ob"):
+              "stencil_select_ob", "stencil_sqdiff_noalloc"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -248,6 +249,17 @@ def stencil_select_ob(times) -> tuple[int, int, float]:
     return s.value, c.value, t.value
 
 
+def stencil_sqdiff_noalloc(a, a_pitch: int, b, nx: int, ny: int, nz: int, out, stream=None) -> None:
+    """out[0] = sum (a-b)^2, out[1] = sum b^2 (FP64, device), with no device allocation.
+    a: FP32 CUDA tensor (row pitch a_pitch), b: FP64 CUDA tensor, out: 2-element FP64 CUDA tensor."""
+    pa, da = _ptr(a)
+    pb, db = _ptr(b)
+    po, do = _ptr(out)
+    if not (da and db and do):
+        raise ValueError("a, b and out must be CUDA tensors")
+    _check(_lib.stencil_sqdiff_noalloc(pa, a_pitch, pb, nx, ny, nz, po, int(stream) if stream else None))
+
+
 def stencil_cfl_limit(radius: int) -> float:
     return float(_lib.stencil_cfl_limit(radius))
 
@@ -292,6 +304,6 @@ EXPORTED = [
     "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
     "stencil_get_stats",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
-    "stencil_candidates_1d", "stencil_select", "stencil_select_ob",
+    "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
     "stencil_version",
 ]
