@@ -110,6 +110,8 @@ _lib.stencil_select.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
 _lib.stencil_select_ob.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, ctypes.POINTER(_I),
                                    ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_sqdiff_noalloc.argtypes = [_P, ctypes.c_int64, _P, _I, _I, _I, _P, _P]
+_lib.stencil_tile_info.argtypes = [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+_lib.stencil_tile_info.restype = ctypes.c_int
 _lib.stencil_cfl_limit.argtypes = [_I]
 _lib.stencil_cfl_limit.restype = ctypes.c_double
 _lib.stencil_last_error.restype = ctypes.c_char_p
@@ -260,6 +262,14 @@ def stencil_sqdiff_noalloc(a, a_pitch: int, b, nx: int, ny: int, nz: int, out, s
     _check(_lib.stencil_sqdiff_noalloc(pa, a_pitch, pb, nx, ny, nz, po, int(stream) if stream else None))
 
 
+def stencil_tile_info(radius: int, tx: int, ty: int):
+    """(smem_bytes, threads) if the tiled kernel is built for this tile, else None."""
+    smem, nt = _I(), _I()
+    if _lib.stencil_tile_info(radius, tx, ty, ctypes.byref(smem), ctypes.byref(nt)):
+        return smem.value, nt.value
+    return None
+
+
 def stencil_cfl_limit(radius: int) -> float:
     return float(_lib.stencil_cfl_limit(radius))
 
@@ -305,5 +315,6 @@ EXPORTED = [
     "stencil_get_stats",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
+    "stencil_tile_info",
     "stencil_version",
 ]

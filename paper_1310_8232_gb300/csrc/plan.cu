@@ -618,6 +618,15 @@ int stencil_rel_l2(stencil_plan_t h, const double *ref, double *out)
 
 double stencil_cfl_limit(int32_t radius) { return cfl_limit(radius); }
 
+int stencil_tile_info(int32_t radius, int32_t tx, int32_t ty, int32_t *smem_bytes, int32_t *threads)
+{
+    int smem = 0, nt = 0, hx = 0;
+    if (!tiled_config(radius, tx, ty, &smem, &nt, &hx)) return 0;
+    if (smem_bytes) *smem_bytes = smem;
+    if (threads) *threads = nt;
+    return 1;
+}
+
 const char *stencil_last_error(void) { return g_last_error.c_str(); }
 
 const char *stencil_version(void) { return "libstencil 0.1.0 (sm_103a)"; }

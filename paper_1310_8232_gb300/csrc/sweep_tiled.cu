@@ -13,7 +13,7 @@ constexpr int SMEM_LIMIT = 227 * 1024;
 template <int R, int TX, int TY>
 struct Inst {
     using S = TiledShape<R, TX, TY>;
-    static constexpr bool fits = S::SMEM <= SMEM_LIMIT;
+    static constexpr bool fits = S::VALID && S::SMEM <= SMEM_LIMIT;
 
     static cudaError_t prepare()
     {
@@ -80,7 +80,7 @@ bool shape_of(int *smem, int *threads, int *hx)
     *smem = S::SMEM;
     *threads = S::NT;
     *hx = S::HX;
-    return S::SMEM <= SMEM_LIMIT;
+    return S::VALID && S::SMEM <= SMEM_LIMIT;
 }
 
 template <int R>

@@ -148,3 +148,13 @@ def test_selection_rejects_bad_arguments(st):
         st.stencil_select(np.ones((1, 1, 1)), 3)
     with pytest.raises(st.StencilError):
         st.stencil_candidates_1d(0, 5)
+
+
+def test_tile_info_reports_built_tiles(st):
+    built = [(tx, ty) for tx in (32, 64, 128) for ty in (4, 8, 16, 32)
+             if st.stencil_tile_info(5, tx, ty) is not None]
+    assert (64, 16) in built
+    smem, threads = st.stencil_tile_info(5, 64, 16)
+    assert 0 < smem <= 227 * 1024 and threads % 32 == 0
+    assert st.stencil_tile_info(5, 48, 16) is None
+    assert st.stencil_tile_info(3, 64, 16) is None
