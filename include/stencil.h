@@ -76,7 +76,9 @@ typedef enum {
 /* Tile parameters of the tiled kernel, the GPU analogue of the paper's
  * blocksize (i, j, k) (Sec. 3, Fig. 1b): tx x ty points of an xy plane per
  * thread block, marching over zchunk planes in z.  tx in {32, 64, 128},
- * ty in {4, 8, 16, 32}; zchunk >= 1 (0 = whole nz). */
+ * ty in {4, 8, 16, 32} (stencil_tile_info says which are built);
+ * zchunk >= 1, 0 = the whole nz, < 0 = chosen by the library from a model
+ * of how the blocks fill the GPU. */
 typedef struct {
     int32_t kernel;     /* stencil_kernel */
     int32_t tx, ty;

@@ -41,5 +41,7 @@ struct TiledMaps {
 // and fits; hx = x-halo width loaded (R rounded up to 16 bytes).
 bool tiled_config(int R, int tx, int ty, int *smem_bytes, int *threads, int *hx);
 cudaError_t launch_tiled(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
+// Resident blocks per SM of the tiled kernel (0 if not built / no device).
+int tiled_blocks_per_sm(int R, int tx, int ty);
 
 }  // namespace stencil

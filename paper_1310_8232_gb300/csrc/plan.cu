@@ -10,6 +10,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
+#include <functional>
 
 #include "internal.h"
 #include "plan_impl.h"
@@ -278,18 +280,56 @@ int Plan::load_velocity(const float *v, int on_device)
     return STENCIL_OK;
 }
 
-int default_zchunk(int nz)
+// Predicted makespan of one sweep with z-chunk zc: blocks (chunk-major,
+// as the hardware hands them out) go to the earliest-free of `slots`
+// resident block slots; a block costs its output planes plus a weight for
+// the 2R warm-up planes, which only stream u.
+static double predicted_makespan(int R, int tiles, int nz, int zc, int slots)
 {
-    return std::min(nz, 64);
+    const double warm = 0.5 * 2 * R;
+    std::vector<double> slot(std::max(1, slots), 0.0);
+    std::make_heap(slot.begin(), slot.end(), std::greater<double>());
+    double makespan = 0;
+    for (int z0 = 0; z0 < nz; z0 += zc) {
+        const double cost = std::min(zc, nz - z0) + warm;
+        for (int t = 0; t < tiles; ++t) {
+            std::pop_heap(slot.begin(), slot.end(), std::greater<double>());
+            slot.back() += cost;
+            makespan = std::max(makespan, slot.back());
+            std::push_heap(slot.begin(), slot.end(), std::greater<double>());
+        }
+    }
+    return makespan;
 }
 
-stencil_tile default_tile(int nz)
+int choose_zchunk(int R, int tx, int ty, int nx, int ny, int nz)
+{
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    const int bps = std::max(1, tiled_blocks_per_sm(R, tx, ty));
+    const int tiles = ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
+    static const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+    int best = nz;
+    double best_t = predicted_makespan(R, tiles, nz, nz, sms * bps);
+    for (int zc : cand) {
+        if (zc >= nz) break;
+        const double t = predicted_makespan(R, tiles, nz, zc, sms * bps);
+        if (t < best_t * (1.0 - 1e-9)) {
+            best_t = t;
+            best = zc;
+        }
+    }
+    return best;
+}
+
+stencil_tile default_tile(int R, int nx, int ny, int nz)
 {
     stencil_tile t;
     t.kernel = STENCIL_KERNEL_TILED;
     t.tx = 64;
     t.ty = 16;
-    t.zchunk = default_zchunk(nz);
+    t.zchunk = choose_zchunk(R, t.tx, t.ty, nx, ny, nz);
     return t;
 }
 
@@ -410,7 +450,9 @@ int plan_create(const stencil_desc *d, Plan **out)
 
     // tile
     stencil_tile t = d->tile;
-    if (t.kernel == STENCIL_KERNEL_AUTO) t = default_tile(d->nz);
+    if (t.kernel == STENCIL_KERNEL_AUTO) t = default_tile(d->radius, d->nx, d->ny, d->nz);
+    else if (t.kernel == STENCIL_KERNEL_TILED && t.zchunk < 0)
+        t.zchunk = choose_zchunk(d->radius, t.tx, t.ty, d->nx, d->ny, d->nz);
     if (t.zchunk == 0) t.zchunk = d->nz;
     rc = check_tile(p->R, t);
     if (rc) return bail(rc);

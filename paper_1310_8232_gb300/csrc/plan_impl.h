@@ -15,7 +15,8 @@ double cfl_limit(int R);
 int64_t row_pitch(int nx);
 int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw, int bh);
 int check_tile(int R, const stencil_tile &t);
-stencil_tile default_tile(int nz);
+stencil_tile default_tile(int R, int nx, int ny, int nz);
+int choose_zchunk(int R, int tx, int ty, int nx, int ny, int nz);
 extern thread_local std::string g_last_error;
 
 struct Plan {

@@ -26,6 +26,20 @@ struct Inst {
         return status;
     }
 
+    static int blocks_per_sm()
+    {
+        if constexpr (!fits) {
+            return 0;
+        } else {
+            if (prepare() != cudaSuccess) return 0;
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tiled_kernel<R, TX, TY>, S::NT, S::SMEM) !=
+                cudaSuccess)
+                return 0;
+            return n;
+        }
+    }
+
     static cudaError_t launch(const TiledMaps &m, const SweepParams &p, cudaStream_t s)
     {
         if constexpr (!fits) {
@@ -73,6 +87,18 @@ cudaError_t launch_tx(int tx, int ty, const TiledMaps &m, const SweepParams &p, 
     }
 }
 
+template <int R>
+int occupancy_r(int tx, int ty)
+{
+#define STENCIL_OCC(TX_, TY_) \
+    if (tx == TX_ && ty == TY_) return Inst<R, TX_, TY_>::blocks_per_sm();
+    STENCIL_OCC(32, 8) STENCIL_OCC(32, 16) STENCIL_OCC(32, 32)
+    STENCIL_OCC(64, 4) STENCIL_OCC(64, 8) STENCIL_OCC(64, 16) STENCIL_OCC(64, 32)
+    STENCIL_OCC(128, 4) STENCIL_OCC(128, 8) STENCIL_OCC(128, 16) STENCIL_OCC(128, 32)
+#undef STENCIL_OCC
+    return 0;
+}
+
 template <int R, int TX, int TY>
 bool shape_of(int *smem, int *threads, int *hx)
 {
@@ -102,6 +128,13 @@ bool tiled_config(int R, int tx, int ty, int *smem, int *threads, int *hx)
     if (R == 4) return config_r<4>(tx, ty, smem, threads, hx);
     if (R == 5) return config_r<5>(tx, ty, smem, threads, hx);
     return false;
+}
+
+int tiled_blocks_per_sm(int R, int tx, int ty)
+{
+    if (R == 4) return occupancy_r<4>(tx, ty);
+    if (R == 5) return occupancy_r<5>(tx, ty);
+    return 0;
 }
 
 cudaError_t launch_tiled(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s)

@@ -347,7 +347,7 @@ int tune_plan(Plan *p, const stencil_desc *d)
         if (mode == STENCIL_TUNE_EXHAUSTIVE) {
             run = cands;
         } else {
-            const int zdef = default_tile(p->nz).zchunk;
+            const int zdef = default_tile(p->R, p->nx, p->ny, p->nz).zchunk;
             for (int tx : TX_VALUES)
                 for (int ty : TY_VALUES)
                     if (feasible(p->R, tx, ty)) run.push_back({tx, ty, zdef});
