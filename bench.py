@@ -36,6 +36,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GPt-updates/s"
 BYTES_PER_POINT = 16            # algorithmic minimum, FP32: u, u_prev, kappa read; u_next written
+# the storage's own minimum: 16-bit u, u_prev, u_next and FP32 kappa
+OWN_BYTES = {"fp32": 16, "fp16": 10, "bf16": 10}
+STORAGE_ID = {"fp32": 0, "fp16": 1, "bf16": 2}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -51,6 +54,8 @@ def parse_args():
     ap.add_argument("--graph", type=int, default=20, help="time steps per captured CUDA graph")
     ap.add_argument("--tile", type=str, default="", help="tx,ty,zchunk of the tiled kernel")
     ap.add_argument("--naive", action="store_true", help="time the one-thread-per-point kernel")
+    ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32",
+                    help="wavefield storage (fp16/bf16: per-plane scaled, FP32 arithmetic)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-timesteps", type=int, default=10)
@@ -255,14 +260,16 @@ def main():
     else:
         tile = None
     desc = st.make_desc(dv, dt, radius=R, dx=workloads.DX, tile=tile, graph_steps=args.graph,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, storage=STORAGE_ID[args.storage])
     t_plan = time.perf_counter()
     plan = st.stencil_plan(desc)
     plan_ms = 1e3 * (time.perf_counter() - t_plan)
     stats = st.stencil_get_stats(plan)
     t = stats.tile
+    etype = {"fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}[args.storage]
     kernel_tag = ("sweep_naive_kernel" if t.kernel == st.STENCIL_KERNEL_NAIVE
-                  else f"sweep_tiled_kernel<{R},{t.tx},{t.ty}>")
+                  else f"sweep_tiled_kernel<{R},{t.tx},{t.ty}>" if args.storage == "fp32"
+                  else f"sweep_tiled_kernel<{R},{t.tx},{t.ty},{etype}>")
 
     def shot():
         st.stencil_set_fields(plan, None, None, 0)
@@ -345,13 +352,17 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(args, {
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
+            "data": "synthetic",
+            "config": workload_config(args, {"storage": args.storage,
                 "tile": {"kernel": kernel_tag, "tx": t.tx, "ty": t.ty, "zchunk": t.zchunk},
                 "graph_steps": args.graph, "plan_ms": plan_ms}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": kernel_tag,
                          "bytes_per_point": BYTES_PER_POINT, "launch_ms": kernel_ms,
+                         "own_bytes_per_point": OWN_BYTES[args.storage],
+                         "own_frac": OWN_BYTES[args.storage] * float(n) ** 3 / (kernel_ms / 1e3) / 1e9 / peak,
                          "peak_source": peak_src, "traffic_source": traffic_src,
                          "timing": "CUDA events around each shot's sweeps on the launching stream; "
                                    "per-launch time = sum / launches (includes the step-counter kernel)"},

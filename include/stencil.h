@@ -269,10 +269,11 @@ STENCIL_API int stencil_sqdiff_noalloc(const float *a, int64_t a_pitch, const do
 
 /* ---- helpers ---------------------------------------------------------- */
 
-/* Whether the tiled kernel is built for (radius, tx, ty); if so *smem_bytes
- * and *threads receive its dynamic shared memory and block size.  Returns 1
- * (available) or 0. */
-STENCIL_API int stencil_tile_info(int32_t radius, int32_t tx, int32_t ty, int32_t *smem_bytes, int32_t *threads);
+/* Whether the tiled kernel is built for (radius, storage, tx, ty); if so
+ * *smem_bytes and *threads receive its dynamic shared memory and block size.
+ * Returns 1 (available) or 0. */
+STENCIL_API int stencil_tile_info(int32_t radius, int32_t storage, int32_t tx, int32_t ty, int32_t *smem_bytes,
+                                  int32_t *threads);
 
 /* Stability bound on v*dt/dx of the 3D leapfrog scheme of radius R:
  * 2 / sqrt(3 W), W = |c_0| + 2 sum |c_r|.  Returns < 0 for an unsupported R. */

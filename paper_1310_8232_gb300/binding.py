@@ -110,7 +110,7 @@ _lib.stencil_select.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
 _lib.stencil_select_ob.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, ctypes.POINTER(_I),
                                    ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_sqdiff_noalloc.argtypes = [_P, ctypes.c_int64, _P, _I, _I, _I, _P, _P]
-_lib.stencil_tile_info.argtypes = [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
+_lib.stencil_tile_info.argtypes = [_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
 _lib.stencil_tile_info.restype = ctypes.c_int
 _lib.stencil_cfl_limit.argtypes = [_I]
 _lib.stencil_cfl_limit.restype = ctypes.c_double
@@ -262,10 +262,10 @@ def stencil_sqdiff_noalloc(a, a_pitch: int, b, nx: int, ny: int, nz: int, out, s
     _check(_lib.stencil_sqdiff_noalloc(pa, a_pitch, pb, nx, ny, nz, po, int(stream) if stream else None))
 
 
-def stencil_tile_info(radius: int, tx: int, ty: int):
+def stencil_tile_info(radius: int, tx: int, ty: int, storage: int = STENCIL_FP32):
     """(smem_bytes, threads) if the tiled kernel is built for this tile, else None."""
     smem, nt = _I(), _I()
-    if _lib.stencil_tile_info(radius, tx, ty, ctypes.byref(smem), ctypes.byref(nt)):
+    if _lib.stencil_tile_info(radius, storage, tx, ty, ctypes.byref(smem), ctypes.byref(nt)):
         return smem.value, nt.value
     return None
 

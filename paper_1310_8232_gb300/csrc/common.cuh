@@ -63,11 +63,17 @@ struct Source {
 // Per-launch parameters of one sweep (one time step) over one grid.
 struct SweepParams {
     int32_t nx, ny, nz;
-    int64_t pitch;                 // row pitch, elements
+    int64_t pitch;                 // row pitch, elements (same for the wavefields and kappa)
     int64_t plane;                 // pitch * ny
-    const float *u;                // u^n
-    float *up;                     // in: u^{n-1}; out: u^{n+1} (in place)
+    const void *u;                 // u^n (FP32, or FP16/BF16 scaled per plane)
+    void *up;                      // in: u^{n-1}; out: u^{n+1} (in place)
     const float *kappa;            // v^2 dt^2 / dx^2
+    // reduced-precision storage only: per-plane power-of-two scales and
+    // amax (float bit patterns) of the time levels, slot = level mod 4
+    float *scale;                  // [4][nz]
+    unsigned *amax;                // [4][nz]
+    float growth;                  // 2 + kappa_max * 3W: bound on |u^{n+1}| / max |u^n| near a point
+    float src_bound;               // |source amplitude|, |w| <= 1
     int32_t zchunk;                // planes per thread block in z
     int32_t tiles_x;               // tiles along x (tiled kernel)
     Source src;

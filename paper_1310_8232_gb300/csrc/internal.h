@@ -31,17 +31,42 @@ cudaError_t launch_sqdiff(const float *a, const double *b, int nx, int ny, int n
 // n += k on the device (step counter between launch chunks)
 cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s);
 
-// ---- K1: 2.5D tiled sweep (TMA-staged xy tile + halo, z register queue) ----
+// ---- K1 / K2: 2.5D tiled sweep (TMA-staged xy tile + halo, z register ring) ----
 struct TiledMaps {
     CUtensorMap u_halo;   // u^n, box (tx + 2 hx) x (ty + 2R) x 1
     CUtensorMap up_core;  // u^{n-1}, box tx x ty x 1
     CUtensorMap k_core;   // kappa, box tx x ty x 1
 };
-// Returns true and the dynamic shared memory size if (R, tx, ty) is built
-// and fits; hx = x-halo width loaded (R rounded up to 16 bytes).
-bool tiled_config(int R, int tx, int ty, int *smem_bytes, int *threads, int *hx);
-cudaError_t launch_tiled(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
-// Resident blocks per SM of the tiled kernel (0 if not built / no device).
-int tiled_blocks_per_sm(int R, int tx, int ty);
+struct TiledInfo {
+    int smem;             // dynamic shared memory, bytes
+    int threads;          // block size
+    int hx;               // x halo loaded on each side (elements)
+    int zmax;             // largest z-chunk (0 = any)
+};
+// storage: 0 FP32, 1 FP16, 2 BF16 (the values of stencil_storage)
+bool tiled_config(int R, int storage, int tx, int ty, TiledInfo *info);
+cudaError_t launch_tiled(int R, int storage, int tx, int ty, const TiledMaps &m, const SweepParams &p,
+                         cudaStream_t s);
+// Resident blocks per SM (0 if not built / no device).
+int tiled_blocks_per_sm(int R, int storage, int tx, int ty);
+
+bool tiled_config_f32(int R, int tx, int ty, TiledInfo *info);
+bool tiled_config_f16(int R, int tx, int ty, TiledInfo *info);
+bool tiled_config_bf16(int R, int tx, int ty, TiledInfo *info);
+int tiled_blocks_per_sm_f32(int R, int tx, int ty);
+int tiled_blocks_per_sm_f16(int R, int tx, int ty);
+int tiled_blocks_per_sm_bf16(int R, int tx, int ty);
+cudaError_t launch_tiled_f32(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
+cudaError_t launch_tiled_f16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
+cudaError_t launch_tiled_bf16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
+
+// ---- K2 helpers: 16-bit fields <-> FP32 with per-plane power-of-two scales ----
+// pack: src FP32 (pitch elements) -> dst 16-bit; writes amax[z] (max |src|
+// over plane z, float bits) and scale[z] (the power of two used).
+cudaError_t launch_pack16(int storage, const float *src, void *dst, int nx, int ny, int nz, int64_t pitch,
+                          float *scale, unsigned *amax, cudaStream_t s);
+// unpack: 16-bit src with scale[z] -> FP32 dst (same pitch)
+cudaError_t launch_unpack16(int storage, const void *src, float *dst, int nx, int ny, int nz, int64_t pitch,
+                            const float *scale, cudaStream_t s);
 
 }  // namespace stencil

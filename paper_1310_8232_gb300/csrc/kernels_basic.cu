@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
     const int z = blockIdx.z;
     if (x >= p.nx) return;
     const int64_t q = (int64_t)z * p.plane + (int64_t)y * p.pitch + x;
-    const float *u = p.u;
+    const float *u = static_cast<const float *>(p.u);
+    float *up = static_cast<float *>(p.up);
     const float c = u[q];
     float acc = 3.0f * wf<R>(0) * c;
 #pragma unroll
@@ -33,12 +34,12 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
         s += (z + r < p.nz) ? u[q + r * p.plane] : 0.0f;
         acc = fmaf(wf<R>(r), s, acc);
     }
-    float nxt = fmaf(p.kappa[q], acc, 2.0f * c - p.up[q]);
+    float nxt = fmaf(p.kappa[q], acc, 2.0f * c - up[q]);
     if (p.src.on && x == p.src.x && y == p.src.y && z == p.src.z) {
         const double t = (double)current_step(p) * p.src.dt;
         nxt += (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
     }
-    p.up[q] = nxt;
+    up[q] = nxt;
 }
 
 cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)

@@ -56,9 +56,38 @@ double cfl_limit(int R)
     return 2.0 / std::sqrt(3.0 * W);
 }
 
-int64_t row_pitch(int nx)
+int64_t row_pitch(int nx, int esize)
 {
-    return ((int64_t)nx + 31) / 32 * 32;   // 128-byte rows for FP32
+    const int64_t per = 128 / esize;       // 128-byte rows for the wavefields
+    return ((int64_t)nx + per - 1) / per * per;
+}
+
+// ---- storage dispatch of the tiled kernel --------------------------------------
+bool tiled_config(int R, int storage, int tx, int ty, TiledInfo *info)
+{
+    TiledInfo tmp;
+    if (!info) info = &tmp;
+    if (storage == STENCIL_FP32) return tiled_config_f32(R, tx, ty, info);
+    if (storage == STENCIL_FP16) return tiled_config_f16(R, tx, ty, info);
+    if (storage == STENCIL_BF16) return tiled_config_bf16(R, tx, ty, info);
+    return false;
+}
+
+int tiled_blocks_per_sm(int R, int storage, int tx, int ty)
+{
+    if (storage == STENCIL_FP32) return tiled_blocks_per_sm_f32(R, tx, ty);
+    if (storage == STENCIL_FP16) return tiled_blocks_per_sm_f16(R, tx, ty);
+    if (storage == STENCIL_BF16) return tiled_blocks_per_sm_bf16(R, tx, ty);
+    return 0;
+}
+
+cudaError_t launch_tiled(int R, int storage, int tx, int ty, const TiledMaps &m, const SweepParams &p,
+                         cudaStream_t s)
+{
+    if (storage == STENCIL_FP32) return launch_tiled_f32(R, tx, ty, m, p, s);
+    if (storage == STENCIL_FP16) return launch_tiled_f16(R, tx, ty, m, p, s);
+    if (storage == STENCIL_BF16) return launch_tiled_bf16(R, tx, ty, m, p, s);
+    return cudaErrorInvalidValue;
 }
 
 // ---- TMA descriptors --------------------------------------------------------
@@ -98,13 +127,14 @@ int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t
 int Plan::build_maps()
 {
     if (tile.kernel != STENCIL_KERNEL_TILED) return STENCIL_OK;
-    int smem, threads, hx;
-    if (!tiled_config(R, tile.tx, tile.ty, &smem, &threads, &hx))
+    TiledInfo info;
+    if (!tiled_config(R, storage, tile.tx, tile.ty, &info))
         return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not built for radius %d", tile.tx, tile.ty, R);
     for (int b = 0; b < 2; ++b) {
-        int rc = encode_map(&maps_halo[b], buf[b], nx, ny, nz, pitch, 4, tile.tx + 2 * hx, tile.ty + 2 * R);
+        int rc = encode_map(&maps_halo[b], buf[b], nx, ny, nz, pitch, esize, tile.tx + 2 * info.hx,
+                            tile.ty + 2 * R);
         if (rc) return rc;
-        rc = encode_map(&maps_core[b], buf[b], nx, ny, nz, pitch, 4, tile.tx, tile.ty);
+        rc = encode_map(&maps_core[b], buf[b], nx, ny, nz, pitch, esize, tile.tx, tile.ty);
         if (rc) return rc;
     }
     return encode_map(&map_kcore, kappa, nx, ny, nz, pitch, 4, tile.tx, tile.ty);
@@ -127,6 +157,10 @@ SweepParams Plan::params(int parity, int step_off) const
     s.step_base = d_step;
     s.step_off = step_off;
     s.err = d_err;
+    s.scale = d_scale;
+    s.amax = d_amax;
+    s.growth = growth;
+    s.src_bound = src_bound;
     return s;
 }
 
@@ -138,7 +172,7 @@ cudaError_t Plan::launch_one(int parity, int step_off, cudaStream_t s) const
     m.u_halo = maps_halo[parity];
     m.up_core = maps_core[parity ^ 1];
     m.k_core = map_kcore;
-    return launch_tiled(R, tile.tx, tile.ty, m, prm, s);
+    return launch_tiled(R, storage, tile.tx, tile.ty, m, prm, s);
 }
 
 int Plan::enqueue_eager(int nsteps)
@@ -237,6 +271,9 @@ void Plan::release()
     drop_graphs();
     for (auto &b : buf)
         if (b) cudaFree(b);
+    for (auto &b : staging)
+        if (b) cudaFree(b);
+    staging[0] = staging[1] = nullptr;
     if (kappa) cudaFree(kappa);
     if (d_scratch) cudaFree(d_scratch);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -276,7 +313,41 @@ int Plan::load_velocity(const float *v, int on_device)
     cfl = (double)vm * dt / dx;
     if (cfl > cfl_lim * (1.0 + 1e-12))
         return fail(STENCIL_ECFL, "vmax*dt/dx = %.6g exceeds the stability bound %.6g", cfl, cfl_lim);
+    // |u^{n+1}| <= (2 + kappa_max * sum |weights|) max|u^n| + |u^{n-1}|; sum
+    // |weights| over the 3D star = 3W with 3W = 4 / cfl_limit^2
+    const double kmax = cfl * cfl;
+    growth = (float)((2.0 + kmax * 4.0 / (cfl_lim * cfl_lim)) * (1.0 + 1e-6));
     velocity_ok = true;
+    return STENCIL_OK;
+}
+
+int Plan::ensure_staging()
+{
+    for (auto &b : staging)
+        if (!b) {
+            cudaError_t e = cudaMalloc(&b, (size_t)field_elems * sizeof(float));
+            if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc(staging)");
+            e = cudaMemsetAsync(b, 0, (size_t)field_elems * sizeof(float), stream);
+            if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync(staging)");
+            device_bytes += field_elems * (int64_t)sizeof(float);
+        }
+    return STENCIL_OK;
+}
+
+int Plan::fp32_level(int which, const float **out)
+{
+    if (storage == STENCIL_FP32) {
+        *out = static_cast<const float *>(buf[cur ^ which]);
+        return STENCIL_OK;
+    }
+    int rc = ensure_staging();
+    if (rc) return rc;
+    const int64_t level = steps_done - which;
+    const int slot = (int)(((level % 4) + 4) % 4);
+    cudaError_t e = launch_unpack16(storage, buf[cur ^ which], staging[which], nx, ny, nz, pitch,
+                                    d_scale + (int64_t)slot * nz, stream);
+    if (e != cudaSuccess) return fail_cuda(e, "unpack");
+    *out = staging[which];
     return STENCIL_OK;
 }
 
@@ -302,34 +373,41 @@ static double predicted_makespan(int R, int tiles, int nz, int zc, int slots)
     return makespan;
 }
 
-int choose_zchunk(int R, int tx, int ty, int nx, int ny, int nz)
+int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz)
 {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-    const int bps = std::max(1, tiled_blocks_per_sm(R, tx, ty));
+    const int bps = std::max(1, tiled_blocks_per_sm(R, storage, tx, ty));
+    TiledInfo info{};
+    tiled_config(R, storage, tx, ty, &info);
+    const int zmax = info.zmax > 0 ? info.zmax : nz;        // 16-bit kernels bound the chunk
     const int tiles = ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
     static const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
-    int best = nz;
-    double best_t = predicted_makespan(R, tiles, nz, nz, sms * bps);
+    int best = 0;
+    double best_t = 0;
+    if (nz <= zmax) {
+        best = nz;
+        best_t = predicted_makespan(R, tiles, nz, nz, sms * bps);
+    }
     for (int zc : cand) {
-        if (zc >= nz) break;
+        if (zc >= nz || zc > zmax) break;
         const double t = predicted_makespan(R, tiles, nz, zc, sms * bps);
-        if (t < best_t * (1.0 - 1e-9)) {
+        if (best == 0 || t < best_t * (1.0 - 1e-9)) {
             best_t = t;
             best = zc;
         }
     }
-    return best;
+    return best > 0 ? best : std::min(nz, zmax);
 }
 
-stencil_tile default_tile(int R, int nx, int ny, int nz)
+stencil_tile default_tile(int R, int storage, int nx, int ny, int nz)
 {
     stencil_tile t;
     t.kernel = STENCIL_KERNEL_TILED;
     t.tx = 64;
     t.ty = 16;
-    t.zchunk = choose_zchunk(R, t.tx, t.ty, nx, ny, nz);
+    t.zchunk = choose_zchunk(R, storage, t.tx, t.ty, nx, ny, nz);
     return t;
 }
 
@@ -349,7 +427,8 @@ int validate_desc(const stencil_desc *d)
             return fail(STENCIL_EINVAL, "source outside the grid");
         if (!(d->src_freq_hz > 0)) return fail(STENCIL_EINVAL, "source frequency must be > 0");
     }
-    if (d->storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "storage %d not built", d->storage);
+    if (d->storage != STENCIL_FP32 && d->storage != STENCIL_FP16 && d->storage != STENCIL_BF16)
+        return fail(STENCIL_EINVAL, "storage must be FP32, FP16 or BF16");
     if (d->graph_steps < 0 || (d->graph_steps & 1))
         return fail(STENCIL_EINVAL, "graph_steps must be 0 or a positive even number");
     if (d->tune_mode < STENCIL_TUNE_NONE || d->tune_mode > STENCIL_TUNE_EXHAUSTIVE)
@@ -357,14 +436,20 @@ int validate_desc(const stencil_desc *d)
     return STENCIL_OK;
 }
 
-int check_tile(int R, const stencil_tile &t)
+int check_tile(int R, int storage, const stencil_tile &t)
 {
-    if (t.kernel == STENCIL_KERNEL_NAIVE) return STENCIL_OK;
+    if (t.kernel == STENCIL_KERNEL_NAIVE) {
+        if (storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "the naive kernel stores FP32 only");
+        return STENCIL_OK;
+    }
     if (t.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EINVAL, "bad kernel id %d", t.kernel);
     if (t.zchunk < 0) return fail(STENCIL_EINVAL, "zchunk must be >= 0");
-    int smem, threads, hx;
-    if (!tiled_config(R, t.tx, t.ty, &smem, &threads, &hx))
-        return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not available for radius %d", t.tx, t.ty, R);
+    TiledInfo info;
+    if (!tiled_config(R, storage, t.tx, t.ty, &info))
+        return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not available for radius %d and storage %d", t.tx, t.ty, R,
+                    storage);
+    if (info.zmax && t.zchunk > info.zmax)
+        return fail(STENCIL_EINVAL, "zchunk %d above %d for 16-bit storage", t.zchunk, info.zmax);
     return STENCIL_OK;
 }
 
@@ -386,7 +471,9 @@ int plan_create(const stencil_desc *d, Plan **out)
     p->nz = d->nz;
     p->dx = d->dx;
     p->dt = d->dt;
-    p->pitch = row_pitch(d->nx);
+    p->storage = d->storage;
+    p->esize = d->storage == STENCIL_FP32 ? 4 : 2;
+    p->pitch = row_pitch(d->nx, p->esize);
     p->field_elems = p->pitch * d->ny * d->nz;
     p->graph_len = d->graph_steps;
     p->tune_mode = d->tune_mode;
@@ -402,15 +489,19 @@ int plan_create(const stencil_desc *d, Plan **out)
         if (e != cudaSuccess) return bail(fail_cuda(e, "cudaStreamCreate"));
         p->own_stream = true;
     }
-    const size_t fbytes = (size_t)p->field_elems * sizeof(float);
+    const size_t fbytes = (size_t)p->field_elems * p->esize;
+    const size_t kbytes = (size_t)p->field_elems * sizeof(float);
     for (auto &b : p->buf) {
         e = cudaMalloc(&b, fbytes);
         if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(field)"));
     }
-    e = cudaMalloc(&p->kappa, fbytes);
+    e = cudaMalloc(&p->kappa, kbytes);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(kappa)"));
-    // scratch: step counter, error word, v range, reduction partials and result
-    const size_t scratch = 256 + sizeof(double) * (2 * RED_BLOCKS + 8);
+    // scratch: step counter, error word, v range, reduction partials and
+    // result, and (16-bit storage) the per-level per-plane scale and amax tables
+    const size_t red_bytes = 256 + sizeof(double) * (2 * RED_BLOCKS + 8);
+    const size_t tab_bytes = p->storage == STENCIL_FP32 ? 0 : (size_t)8 * 4 * d->nz;
+    const size_t scratch = red_bytes + tab_bytes;
     e = cudaMalloc(&p->d_scratch, scratch);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(scratch)"));
     unsigned char *sc = static_cast<unsigned char *>(p->d_scratch);
@@ -420,13 +511,17 @@ int plan_create(const stencil_desc *d, Plan **out)
     p->d_bad = reinterpret_cast<unsigned long long *>(sc + 24);
     p->d_result = reinterpret_cast<double *>(sc + 64);
     p->d_partials = reinterpret_cast<double *>(sc + 256);
-    p->device_bytes = 3 * (int64_t)fbytes + (int64_t)scratch;
+    if (tab_bytes) {
+        p->d_scale = reinterpret_cast<float *>(sc + red_bytes);
+        p->d_amax = reinterpret_cast<unsigned *>(sc + red_bytes + 4 * 4 * (size_t)d->nz);
+    }
+    p->device_bytes = 2 * (int64_t)fbytes + (int64_t)kbytes + (int64_t)scratch;
 
     cudaStream_t s = p->stream;
     if ((e = cudaMemsetAsync(p->d_scratch, 0, scratch, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->buf[0], 0, fbytes, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->buf[1], 0, fbytes, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->kappa, 0, fbytes, s)) != cudaSuccess)
+        (e = cudaMemsetAsync(p->kappa, 0, kbytes, s)) != cudaSuccess)
         return bail(fail_cuda(e, "cudaMemsetAsync"));
     float v_src = 0.0f;
     if (d->src_amp != 0.0) {
@@ -447,14 +542,15 @@ int plan_create(const stencil_desc *d, Plan **out)
     p->src.t0 = d->src_t0 < 0 ? 1.0 / d->src_freq_hz : d->src_t0;
     p->src.dt = d->dt;
     p->src.scale = d->src_amp * (double)v_src * (double)v_src * d->dt * d->dt;
+    p->src_bound = (float)(std::fabs(p->src.scale) * (1.0 + 1e-6));
 
     // tile
     stencil_tile t = d->tile;
-    if (t.kernel == STENCIL_KERNEL_AUTO) t = default_tile(d->radius, d->nx, d->ny, d->nz);
+    if (t.kernel == STENCIL_KERNEL_AUTO) t = default_tile(d->radius, d->storage, d->nx, d->ny, d->nz);
     else if (t.kernel == STENCIL_KERNEL_TILED && t.zchunk < 0)
-        t.zchunk = choose_zchunk(d->radius, t.tx, t.ty, d->nx, d->ny, d->nz);
+        t.zchunk = choose_zchunk(d->radius, d->storage, t.tx, t.ty, d->nx, d->ny, d->nz);
     if (t.zchunk == 0) t.zchunk = d->nz;
-    rc = check_tile(p->R, t);
+    rc = check_tile(p->R, p->storage, t);
     if (rc) return bail(rc);
     p->tile = t;
     rc = p->build_maps();
@@ -520,8 +616,11 @@ int stencil_step(stencil_plan_t h, int32_t nsteps)
     return p->enqueue(nsteps);
 }
 
-static int copy_out(Plan *p, const float *src, float *out, int on_device)
+static int copy_out(Plan *p, int which, float *out, int on_device)
 {
+    const float *src = nullptr;
+    int rc = p->fp32_level(which, &src);
+    if (rc) return rc;
     cudaError_t e = cudaMemcpy2DAsync(out, (size_t)p->nx * sizeof(float), src, p->pitch * sizeof(float),
                                       (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream);
@@ -537,7 +636,7 @@ int stencil_run(stencil_plan_t h, int32_t nsteps, float *out_u, int32_t out_on_d
     int rc = p->enqueue(nsteps);
     if (rc) return rc;
     if (out_u) {
-        rc = copy_out(p, p->buf[p->cur], out_u, out_on_device);
+        rc = copy_out(p, 0, out_u, out_on_device);
         if (rc) return rc;
     }
     return p->check_device_error();
@@ -557,7 +656,7 @@ int stencil_get_field(stencil_plan_t h, int32_t which, float *out, int32_t out_o
     if (which != 0 && which != 1) return fail(STENCIL_EINVAL, "which must be 0 or 1");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
-    int rc = copy_out(p, p->buf[p->cur ^ which], out, out_on_device);
+    int rc = copy_out(p, which, out, out_on_device);
     if (rc) return rc;
     return p->check_device_error();
 }
@@ -569,16 +668,40 @@ int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, in
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
     const float *src[2] = {u, u_prev};
+    if (p->storage != STENCIL_FP32) {
+        int rc = p->ensure_staging();
+        if (rc) return rc;
+    }
     for (int k = 0; k < 2; ++k) {
-        float *dst = p->buf[p->cur ^ k];
+        void *dst = p->buf[p->cur ^ k];
+        const int64_t level = step - k;
+        const int slot = (int)(((level % 4) + 4) % 4);
         cudaError_t e;
-        if (src[k])
-            e = cudaMemcpy2DAsync(dst, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
+        if (!src[k]) {
+            e = cudaMemsetAsync(dst, 0, (size_t)p->field_elems * p->esize, p->stream);
+            if (e == cudaSuccess && p->d_amax)
+                e = cudaMemsetAsync(p->d_amax + (int64_t)slot * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
+            if (e == cudaSuccess && p->d_scale)
+                e = cudaMemsetAsync(p->d_scale + (int64_t)slot * p->nz, 0, sizeof(float) * p->nz, p->stream);
+        } else {
+            float *stage = p->storage == STENCIL_FP32 ? static_cast<float *>(dst) : p->staging[0];
+            e = cudaMemcpy2DAsync(stage, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
                                   (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream);
-        else
-            e = cudaMemsetAsync(dst, 0, (size_t)p->field_elems * sizeof(float), p->stream);
+            if (e == cudaSuccess && p->storage != STENCIL_FP32)
+                e = launch_pack16(p->storage, stage, dst, p->nx, p->ny, p->nz, p->pitch,
+                                  p->d_scale + (int64_t)slot * p->nz, p->d_amax + (int64_t)slot * p->nz, p->stream);
+        }
         if (e != cudaSuccess) return fail_cuda(e, "field copy in");
+    }
+    if (p->d_amax) {
+        // the slots the next two steps write must start from zero
+        for (int64_t level = step + 1; level <= step + 2; ++level) {
+            const int slot = (int)(level % 4);
+            cudaError_t e =
+                cudaMemsetAsync(p->d_amax + (int64_t)slot * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
+            if (e != cudaSuccess) return fail_cuda(e, "amax reset");
+        }
     }
     cudaError_t e = cudaMemcpyAsync(p->d_step, &step, sizeof step, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "step counter copy");
@@ -601,7 +724,8 @@ int stencil_set_velocity(stencil_plan_t h, const float *velocity, int32_t on_dev
     int rc = p->load_velocity(velocity, on_device);
     if (rc) return rc;
     p->src.scale = p->src_amp * (double)v_src * (double)v_src * p->dt * p->dt;
-    p->drop_graphs();   // captured launches carry the old source scale
+    p->src_bound = (float)(std::fabs(p->src.scale) * (1.0 + 1e-6));
+    p->drop_graphs();   // captured launches carry the old source scale and growth bound
     return STENCIL_OK;
 }
 
@@ -616,7 +740,7 @@ int stencil_get_stats(stencil_plan_t h, stencil_stats *s)
     s->cfl = p->cfl;
     s->cfl_limit = p->cfl_lim;
     s->pitch = p->pitch;
-    s->field_bytes = p->field_elems * (int64_t)sizeof(float);
+    s->field_bytes = p->field_elems * (int64_t)p->esize;
     s->device_bytes = p->device_bytes;
     s->min_time_ms = p->min_time_ms;
     s->actual_time_ms = p->actual_time_ms;
@@ -633,8 +757,12 @@ int stencil_energy(stencil_plan_t h, double *out)
     if (!h || !out) return fail(STENCIL_EINVAL, "null argument");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
-    cudaError_t e = launch_energy(p->R, p->buf[p->cur], p->buf[p->cur ^ 1], p->kappa, p->nx, p->ny, p->nz, p->pitch,
-                                  p->d_partials, p->d_result, p->stream);
+    const float *u1 = nullptr, *u0 = nullptr;
+    int rc = p->fp32_level(0, &u1);
+    if (!rc) rc = p->fp32_level(1, &u0);
+    if (rc) return rc;
+    cudaError_t e = launch_energy(p->R, u1, u0, p->kappa, p->nx, p->ny, p->nz, p->pitch, p->d_partials,
+                                  p->d_result, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "energy");
     e = cudaMemcpyAsync(out, p->d_result, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "energy copy");
@@ -646,8 +774,10 @@ int stencil_rel_l2(stencil_plan_t h, const double *ref, double *out)
     if (!h || !ref || !out) return fail(STENCIL_EINVAL, "null argument");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
-    cudaError_t e = launch_sqdiff(p->buf[p->cur], ref, p->nx, p->ny, p->nz, p->pitch, p->d_partials, p->d_result,
-                                  p->stream);
+    const float *u1 = nullptr;
+    int rc0 = p->fp32_level(0, &u1);
+    if (rc0) return rc0;
+    cudaError_t e = launch_sqdiff(u1, ref, p->nx, p->ny, p->nz, p->pitch, p->d_partials, p->d_result, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "rel_l2");
     double h2[2];
     e = cudaMemcpyAsync(h2, p->d_result, sizeof h2, cudaMemcpyDeviceToHost, p->stream);
@@ -660,12 +790,13 @@ int stencil_rel_l2(stencil_plan_t h, const double *ref, double *out)
 
 double stencil_cfl_limit(int32_t radius) { return cfl_limit(radius); }
 
-int stencil_tile_info(int32_t radius, int32_t tx, int32_t ty, int32_t *smem_bytes, int32_t *threads)
+int stencil_tile_info(int32_t radius, int32_t storage, int32_t tx, int32_t ty, int32_t *smem_bytes,
+                      int32_t *threads)
 {
-    int smem = 0, nt = 0, hx = 0;
-    if (!tiled_config(radius, tx, ty, &smem, &nt, &hx)) return 0;
-    if (smem_bytes) *smem_bytes = smem;
-    if (threads) *threads = nt;
+    TiledInfo info;
+    if (!tiled_config(radius, storage, tx, ty, &info)) return 0;
+    if (smem_bytes) *smem_bytes = info.smem;
+    if (threads) *threads = info.threads;
     return 1;
 }
 

@@ -12,11 +12,11 @@ namespace stencil {
 int fail(int code, const char *fmt, ...);
 int fail_cuda(cudaError_t e, const char *what);
 double cfl_limit(int R);
-int64_t row_pitch(int nx);
+int64_t row_pitch(int nx, int esize);
 int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw, int bh);
-int check_tile(int R, const stencil_tile &t);
-stencil_tile default_tile(int R, int nx, int ny, int nz);
-int choose_zchunk(int R, int tx, int ty, int nx, int ny, int nz);
+stencil_tile default_tile(int R, int storage, int nx, int ny, int nz);
+int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz);
+int check_tile(int R, int storage, const stencil_tile &t);
 extern thread_local std::string g_last_error;
 
 struct Plan {
@@ -26,10 +26,16 @@ struct Plan {
     int R = 5;
     int nx = 0, ny = 0, nz = 0;
     double dx = 0, dt = 0;
-    int64_t pitch = 0;
+    int64_t pitch = 0;                    // row pitch in elements (wavefields and kappa)
     int64_t field_elems = 0;
-    float *buf[2] = {nullptr, nullptr};   // buf[cur] = u^n, buf[cur ^ 1] = u^{n-1}
+    int storage = STENCIL_FP32;
+    int esize = 4;                        // bytes per wavefield element
+    void *buf[2] = {nullptr, nullptr};    // buf[cur] = u^n, buf[cur ^ 1] = u^{n-1}
     float *kappa = nullptr;
+    float *staging[2] = {nullptr, nullptr};   // 16-bit storage: FP32 copies for state transfer
+    float *d_scale = nullptr;             // 16-bit storage: [4][nz] per-plane scales by level mod 4
+    unsigned *d_amax = nullptr;           // 16-bit storage: [4][nz] per-plane max |u| by level mod 4
+    float growth = 0, src_bound = 0;
     int cur = 0;
     void *d_scratch = nullptr;
     int64_t *d_step = nullptr;
@@ -55,6 +61,11 @@ struct Plan {
     double min_time_ms = NAN, actual_time_ms = NAN, full_time_ms = NAN, quality = NAN, selection_ms = NAN;
     int n_candidates = 0;
 
+    char *bptr(int b, int64_t off_elems) const { return static_cast<char *>(buf[b]) + off_elems * esize; }
+    int ensure_staging();
+    // FP32 view of level n - which (the field itself for FP32 storage, an
+    // unpacked copy in staging[which] for 16-bit storage); enqueued on stream
+    int fp32_level(int which, const float **out);
     int build_maps();
     int load_velocity(const float *v, int on_device);
     SweepParams params(int parity, int step_off) const;

@@ -1,4 +1,6 @@
-// K1: 2.5D-blocked sweep, one time step per launch.
+// K1 / K2: 2.5D-blocked sweep, one time step per launch; wavefields stored
+// in FP32 (K1) or in FP16 / BF16 with a power-of-two scale per z plane and
+// time level (K2); the arithmetic is FP32 either way.
 //
 // The GPU form of the paper's loop tiling (Sec. 3, Fig. 1b): instead of a
 // cache blocksize (i, j, k) each thread block owns a TX x TY tile of the xy
@@ -9,16 +11,16 @@
 //   * TMA boxes of u^{n-1} and kappa (TX x TY) land in a ring of SA stages;
 //   * each thread owns 4 consecutive x points in each of 2 rows (the y
 //     neighbours it loads serve both rows).  When plane p lands, the thread
-//     reads its own values and its x and y neighbours (16-byte shared-memory
+//     reads its own values and its x and y neighbours (shared-memory
 //     vectors) and immediately forms the partial sum of output plane p: x
 //     and y terms, the z centre and the z terms of the R planes below p,
 //     which it keeps in registers.  Plane p also adds its z term to the
 //     partial sums of the R-1 outputs below it and completes output p-R,
-//     which is then updated with u^{n-1} and kappa and written over u^{n-1}
-//     with 16-byte stores.  A u stage is therefore free again right after
-//     its plane has been read, so shared memory holds copies in flight
-//     rather than planes waiting for their turn, and a small footprint
-//     (4 stages) lets three blocks share an SM;
+//     which is then updated with u^{n-1} and kappa and written over u^{n-1}.
+//     A u stage is therefore free again right after its plane has been read,
+//     so shared memory holds copies in flight rather than planes waiting for
+//     their turn, and a small footprint (4 stages) lets three blocks share an
+//     SM;
 //   * arithmetic runs two points at a time with packed FP32 instructions;
 //     the register ring of (u, partial) pairs is rotated by unrolling.
 // Thread 0 issues every copy right after the block barrier that ends each
@@ -26,7 +28,18 @@
 // signal arrival.  Every wait is bounded: a stuck wait sets ERR_TIMEOUT and
 // the whole block leaves at the next barrier, after the copies it issued
 // have landed (also bounded).
+//
+// 16-bit storage: a stored value h of plane z at level n means h * s_n[z],
+// s a power of two (so scaling is exact).  The scale of each output plane
+// is fixed before anything is written, from a bound every block computes the
+// same way: |u^{n+1}| <= g * max|u^n| over planes z-R..z+R + max|u^{n-1}|
+// at z (+ the source amplitude on the source plane), g = 2 + kappa_max * 3W,
+// and the stored magnitudes are kept below 2^15.  Each block reduces
+// max|u^{n+1}| of its tile per plane and merges it with one atomicMax.
 #pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <type_traits>
 
@@ -34,9 +47,57 @@
 
 namespace stencil {
 
-template <int R, int TX, int TY>
+// ---- element access ----------------------------------------------------------------
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float4 ld4(const __half *p)
+{
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&v.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p)
+{
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st4(float *p, const float4 &v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void st4(__half *p, const float4 &v)
+{
+    const __half2 a = __floats2half2_rn(v.x, v.y);
+    const __half2 b = __floats2half2_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&a);
+    u.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, const float4 &v)
+{
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<const unsigned *>(&a);
+    u.y = *reinterpret_cast<const unsigned *>(&b);
+    *reinterpret_cast<uint2 *>(p) = u;
+}
+
+// Smallest power of two s >= 2^-126 with b / s <= 2^15 (1 for b == 0).
+__device__ __forceinline__ float pow2_scale(float b)
+{
+    if (!(b > 0.0f)) return 1.0f;
+    if (!isfinite(b)) return ldexpf(1.0f, 127);
+    int e;
+    frexpf(b, &e);                 // b = f * 2^e, f in [0.5, 1): b < 2^e
+    return ldexpf(1.0f, max(e - 15, -126));
+}
+
+template <int R, int TX, int TY, typename E>
 struct TiledShape {
-    static constexpr int HX = ((R + 3) / 4) * 4;        // x halo rounded to 16 bytes
+    static constexpr bool F32 = std::is_same<E, float>::value;
+    static constexpr int ES = sizeof(E);
+    static constexpr int HX = F32 ? ((R + 3) / 4) * 4 : 8;   // x halo rounded to 16 bytes
     static constexpr int BW = TX + 2 * HX;              // u box width
     static constexpr int BH = TY + 2 * R;               // u box height
     static constexpr int TPR = TX / 4;                  // threads per row
@@ -45,11 +106,20 @@ struct TiledShape {
     static constexpr int RING = R + 1;                  // register ring of (u, partial) per plane
     static constexpr int SU = 4;                        // u stages: 1 being read + 3 in flight
     static constexpr int SA = 4;                        // u_prev / kappa stages
-    static constexpr int U_ELEMS = ((BW * BH * 4 + 127) / 128) * 32;   // stage size in floats (128 B aligned)
-    static constexpr int A_ELEMS = TX * TY;
-    static constexpr uint32_t U_BYTES = BW * BH * 4;
-    static constexpr uint32_t A_BYTES = TX * TY * 4;
-    static constexpr int BAR_OFF = (SU * U_ELEMS + 2 * SA * A_ELEMS) * 4;
+    static constexpr int ZMAX = F32 ? 0 : 256;          // largest z-chunk (16-bit: scale tables)
+    static constexpr uint32_t U_BYTES = BW * BH * ES;
+    static constexpr uint32_t P_BYTES = TX * TY * ES;
+    static constexpr uint32_t K_BYTES = TX * TY * 4;
+    static constexpr int U_STAGE = ((U_BYTES + 127) / 128) * 128;
+    static constexpr int P_STAGE = ((P_BYTES + 127) / 128) * 128;
+    static constexpr int K_STAGE = K_BYTES;
+    static constexpr int P_OFF = SU * U_STAGE;
+    static constexpr int K_OFF = P_OFF + SA * P_STAGE;
+    static constexpr int SIG_OFF = K_OFF + SA * K_STAGE;
+    // 16-bit: scales of the planes entering the ring, of u^{n-1} and of the
+    // outputs, plus per-warp maxima (double-buffered by plane parity)
+    static constexpr int SIG_BYTES = F32 ? 0 : ((ZMAX + 2 * R) + 2 * ZMAX + 2 * (NT / 32)) * 4;
+    static constexpr int BAR_OFF = ((SIG_OFF + SIG_BYTES + 15) / 16) * 16;
     static constexpr int FLAG_OFF = BAR_OFF + (SU + SA) * 8;
     static constexpr int SMEM = FLAG_OFF + 16;
     static_assert(TX % 32 == 0 && TX >= 32 && BW <= 256 && BH <= 256, "TMA box limits");
@@ -77,17 +147,28 @@ struct Unroll<N, N> {
 
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float4 scale4(const float4 &v, float s)
+{
+    const float2 ss = make_float2(s, s);
+    const float2 a = __fmul2_rn(lo2(v), ss);
+    const float2 b = __fmul2_rn(hi2(v), ss);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
 
-template <int R, int TX, int TY>
-__global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
+template <int R, int TX, int TY, typename E>
+__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
     sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,
                        const __grid_constant__ CUtensorMap map_k, const SweepParams p)
 {
-    using S = TiledShape<R, TX, TY>;
+    using S = TiledShape<R, TX, TY, E>;
     extern __shared__ __align__(128) unsigned char smem[];
-    float *su = reinterpret_cast<float *>(smem);
-    float *sp = su + S::SU * S::U_ELEMS;
-    float *sk = sp + S::SA * S::A_ELEMS;
+    unsigned char *su = smem;
+    unsigned char *sp = smem + S::P_OFF;
+    unsigned char *sk = smem + S::K_OFF;
+    float *sig_in = reinterpret_cast<float *>(smem + S::SIG_OFF);   // [ZMAX + 2R]: s_n of planes pz0 + j
+    float *sig_prev = sig_in + (S::ZMAX + 2 * R);                    // [ZMAX]: s_{n-1} of outputs z0 + j
+    float *sig_out = sig_prev + S::ZMAX;                             // [ZMAX]: s_{n+1} of outputs z0 + j
+    unsigned *wmax = reinterpret_cast<unsigned *>(sig_out + S::ZMAX);   // [2][NT/32]
     uint64_t *full_u = reinterpret_cast<uint64_t *>(smem + S::BAR_OFF);
     uint64_t *full_a = full_u + S::SU;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + S::FLAG_OFF);
@@ -107,13 +188,13 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
     auto issue_u = [&](int t) {               // plane pz0 + t into stage t % SU
         const int st = t % S::SU;
         mbar_arrive_expect_tx(&full_u[st], S::U_BYTES);
-        tma_load_3d(su + st * S::U_ELEMS, &map_u, &full_u[st], x0 - S::HX, y0 - R, pz0 + t);
+        tma_load_3d(su + st * S::U_STAGE, &map_u, &full_u[st], x0 - S::HX, y0 - R, pz0 + t);
     };
     auto issue_a = [&](int ja) {              // u^{n-1} and kappa of output z0 + ja into stage ja % SA
         const int st = ja % S::SA;
-        mbar_arrive_expect_tx(&full_a[st], 2 * S::A_BYTES);
-        tma_load_3d(sp + st * S::A_ELEMS, &map_up, &full_a[st], x0, y0, z0 + ja);
-        tma_load_3d(sk + st * S::A_ELEMS, &map_k, &full_a[st], x0, y0, z0 + ja);
+        mbar_arrive_expect_tx(&full_a[st], S::P_BYTES + S::K_BYTES);
+        tma_load_3d(sp + st * S::P_STAGE, &map_up, &full_a[st], x0, y0, z0 + ja);
+        tma_load_3d(sk + st * S::K_STAGE, &map_k, &full_a[st], x0, y0, z0 + ja);
     };
 
     if (tid == 0) {
@@ -124,6 +205,38 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
         for (int t = 0; t < S::SU && t < nin; ++t) issue_u(t);
         for (int ja = 0; ja < S::SA && ja < nout; ++ja) issue_a(ja);
     }
+    int slot_out = 0;                         // 16-bit: slot of level n+1 in scale/amax
+    if constexpr (!S::F32) {
+        // scales of this block's planes, and those of its outputs (every block
+        // computes the same value; tile 0 of each z-chunk publishes them)
+        const int64_t n = current_step(p);
+        const int s_n = (int)(n & 3), s_p = (int)((n + 3) & 3);
+        slot_out = (int)((n + 1) & 3);
+        const int s_clear = (int)((n + 2) & 3);
+        const float *scale_n = p.scale + (int64_t)s_n * p.nz;
+        const float *scale_p = p.scale + (int64_t)s_p * p.nz;
+        const unsigned *amax_n = p.amax + (int64_t)s_n * p.nz;
+        const unsigned *amax_p = p.amax + (int64_t)s_p * p.nz;
+        for (int j = tid; j < nin; j += S::NT) {
+            const int z = pz0 + j;
+            sig_in[j] = (z >= 0 && z < p.nz) ? scale_n[z] : 1.0f;
+        }
+        for (int j = tid; j < nout; j += S::NT) {
+            const int o = z0 + j;
+            sig_prev[j] = scale_p[o];
+            float m = 0.0f;
+            for (int d = -R; d <= R; ++d)
+                if (o + d >= 0 && o + d < p.nz) m = fmaxf(m, __uint_as_float(amax_n[o + d]));
+            float b = p.growth * m + __uint_as_float(amax_p[o]);
+            if (p.src.on && o == p.src.z) b += p.src_bound;
+            const float sg = pow2_scale(b);
+            sig_out[j] = sg;
+            if (blockIdx.x == 0) p.scale[(int64_t)slot_out * p.nz + o] = sg;
+        }
+        // level n-2's slot becomes level n+2's: clear it for the next step
+        if (blockIdx.x == 0 && blockIdx.y == 0)
+            for (int z = tid; z < p.nz; z += S::NT) p.amax[(int64_t)s_clear * p.nz + z] = 0u;
+    }
     __syncthreads();
 
     const int tx4 = tid % S::TPR;
@@ -131,9 +244,9 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
     const int gx = x0 + 4 * tx4;
     const int gy0 = y0 + ty0;
     const bool x_ok = gx < p.nx;
-    const int own = (R + ty0) * S::BW + S::HX + 4 * tx4;   // own 4 points of row 0 in a u stage
+    const int own = (R + ty0) * S::BW + S::HX + 4 * tx4;   // own 4 points of row 0 in a u stage (elements)
     const int own_a = ty0 * TX + 4 * tx4;
-    float *dst = p.up + (int64_t)gy0 * p.pitch + gx;
+    E *dst = static_cast<E *>(p.up) + (int64_t)gy0 * p.pitch + gx;
     const int src_row = p.src.y - gy0;                     // this thread's row holding the source, if any
     const bool src_here = p.src.on && (unsigned)src_row < (unsigned)S::ROWS && (unsigned)(p.src.x - gx) < 4u &&
                           p.src.z >= z0 && p.src.z < z1;
@@ -164,11 +277,13 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
             const int i = i0 + K;
             if (i >= nin) return;                           // block-uniform
             if (!mbar_wait(&full_u[su_stage], su_phase, p.err)) *abort_flag = 1;
-            const float *pl = su + su_stage * S::U_ELEMS + own;
+            const E *pl = reinterpret_cast<const E *>(su + su_stage * S::U_STAGE) + own;
+            const float sgi = S::F32 ? 1.0f : sig_in[i];
             // column of the thread's x group: rows -R .. ROWS-1+R around row 0
+            // (stored units; scaled to true values where they enter the sums)
             float4 col[S::ROWS + 2 * R];
 #pragma unroll
-            for (int h = 0; h < S::ROWS; ++h) col[R + h] = *reinterpret_cast<const float4 *>(pl + h * S::BW);
+            for (int h = 0; h < S::ROWS; ++h) col[R + h] = ld4(pl + h * S::BW);
             float2 nA[S::ROWS], nB[S::ROWS];
 #pragma unroll
             for (int h = 0; h < S::ROWS; ++h) {
@@ -179,26 +294,27 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
                 // partial sums of output plane i: centre, x, y, and z below
 #pragma unroll
                 for (int r = 1; r <= R; ++r) {
-                    col[R - r] = *reinterpret_cast<const float4 *>(pl - r * S::BW);
-                    col[R + S::ROWS - 1 + r] = *reinterpret_cast<const float4 *>(pl + (S::ROWS - 1 + r) * S::BW);
+                    col[R - r] = ld4(pl - r * S::BW);
+                    col[R + S::ROWS - 1 + r] = ld4(pl + (S::ROWS - 1 + r) * S::BW);
                 }
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) {
-                    const float *ph = pl + h * S::BW;
+                    const E *ph = pl + h * S::BW;
                     const float4 c = col[R + h];
                     float2 aA = __fmul2_rn(c0x3, lo2(c));
                     float2 aB = __fmul2_rn(c0x3, hi2(c));
+                    float2 zA = make_float2(0.f, 0.f), zB = make_float2(0.f, 0.f);   // 16-bit: z terms
                     // row[m] = u[gx - 8 + m], m = 0..19; own points are m = 8..11
                     float row[20];
                     {
-                        const float4 l1 = *reinterpret_cast<const float4 *>(ph - 4);
-                        const float4 r1 = *reinterpret_cast<const float4 *>(ph + 4);
+                        const float4 l1 = ld4(ph - 4);
+                        const float4 r1 = ld4(ph + 4);
                         row[4] = l1.x; row[5] = l1.y; row[6] = l1.z; row[7] = l1.w;
                         row[8] = c.x; row[9] = c.y; row[10] = c.z; row[11] = c.w;
                         row[12] = r1.x; row[13] = r1.y; row[14] = r1.z; row[15] = r1.w;
                         if constexpr (R > 4) {
-                            const float4 l2 = *reinterpret_cast<const float4 *>(ph - 8);
-                            const float4 r2 = *reinterpret_cast<const float4 *>(ph + 8);
+                            const float4 l2 = ld4(ph - 8);
+                            const float4 r2 = ld4(ph + 8);
                             row[0] = l2.x; row[1] = l2.y; row[2] = l2.z; row[3] = l2.w;
                             row[16] = r2.x; row[17] = r2.y; row[18] = r2.z; row[19] = r2.w;
                         } else {
@@ -210,22 +326,37 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
                     for (int r = 1; r <= R; ++r) {
                         const float4 ym = col[R + h - r];
                         const float4 yp = col[R + h + r];
-                        const float4 zm = uq[h][(K + S::RING - r) % S::RING];   // plane i - r
+                        const float4 zm = uq[h][(K + S::RING - r) % S::RING];   // plane i - r (true values)
                         float2 sA =
                             __fadd2_rn(make_float2(row[8 - r], row[9 - r]), make_float2(row[8 + r], row[9 + r]));
                         float2 sB =
                             __fadd2_rn(make_float2(row[10 - r], row[11 - r]), make_float2(row[10 + r], row[11 + r]));
                         sA = __fadd2_rn(sA, __fadd2_rn(lo2(ym), lo2(yp)));
                         sB = __fadd2_rn(sB, __fadd2_rn(hi2(ym), hi2(yp)));
-                        sA = __fadd2_rn(sA, lo2(zm));
-                        sB = __fadd2_rn(sB, hi2(zm));
                         const float2 cr = make_float2(wf<R>(r), wf<R>(r));
+                        if constexpr (S::F32) {
+                            sA = __fadd2_rn(sA, lo2(zm));
+                            sB = __fadd2_rn(sB, hi2(zm));
+                        } else {
+                            zA = __ffma2_rn(cr, lo2(zm), zA);
+                            zB = __ffma2_rn(cr, hi2(zm), zB);
+                        }
                         aA = __ffma2_rn(cr, sA, aA);
                         aB = __ffma2_rn(cr, sB, aB);
+                    }
+                    if constexpr (!S::F32) {
+                        // stored units -> true values: (x, y, centre) * s_n + z terms
+                        const float2 ss = make_float2(sgi, sgi);
+                        aA = __ffma2_rn(ss, aA, zA);
+                        aB = __ffma2_rn(ss, aB, zB);
                     }
                     nA[h] = aA;
                     nB[h] = aB;
                 }
+            }
+            if constexpr (!S::F32) {
+#pragma unroll
+                for (int h = 0; h < S::ROWS; ++h) col[R + h] = scale4(col[R + h], sgi);
             }
             if (++su_stage == S::SU) {
                 su_stage = 0;
@@ -246,18 +377,23 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
                 // ... and the last one above output i - R, which is now complete
                 constexpr int KF = (K + 1) % S::RING;             // slot of plane i - R
                 const float2 cR = make_float2(wf<R>(R), wf<R>(R));
+                const int ja = i - 2 * R;
                 if (!mbar_wait(&full_a[sa_stage], sa_phase, p.err)) *abort_flag = 1;
+                const float sgp = S::F32 ? 1.0f : sig_prev[ja];
                 float4 prev[S::ROWS], kap[S::ROWS];
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) {
-                    prev[h] = *reinterpret_cast<const float4 *>(sp + sa_stage * S::A_ELEMS + own_a + h * TX);
-                    kap[h] = *reinterpret_cast<const float4 *>(sk + sa_stage * S::A_ELEMS + own_a + h * TX);
+                    prev[h] = ld4(reinterpret_cast<const E *>(sp + sa_stage * S::P_STAGE) + own_a + h * TX);
+                    if constexpr (!S::F32) prev[h] = scale4(prev[h], sgp);
+                    kap[h] = ld4(reinterpret_cast<const float *>(sk + sa_stage * S::K_STAGE) + own_a + h * TX);
                 }
                 if (++sa_stage == S::SA) {
                     sa_stage = 0;
                     sa_phase ^= 1;
                 }
-                const int o = z0 + (i - 2 * R);
+                const int o = z0 + ja;
+                const float inv_out = S::F32 ? 1.0f : 1.0f / sig_out[ja];   // exact: a power of two
+                float omax = 0.0f;
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) {
                     const float4 c = col[R + h];
@@ -279,8 +415,18 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
                         else if (k == 2) nxt.z += add;
                         else nxt.w += add;
                     }
-                    if (x_ok && gy0 + h < p.ny)
-                        *reinterpret_cast<float4 *>(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane) = nxt;
+                    const bool ok = x_ok && gy0 + h < p.ny;
+                    if constexpr (!S::F32) {
+                        if (ok)
+                            omax = fmaxf(omax, fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)),
+                                                     fmaxf(fabsf(nxt.z), fabsf(nxt.w))));
+                        nxt = scale4(nxt, inv_out);
+                    }
+                    if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
+                }
+                if constexpr (!S::F32) {
+                    const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
+                    if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
                 }
             }
             // slot K held plane i - R - 1, which nothing needs any more
@@ -301,6 +447,13 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY>::NT)
             if (tid == 0) {
                 if (i + S::SU < nin) issue_u(i + S::SU);
                 if (i >= 2 * R && i - 2 * R + S::SA < nout) issue_a(i - 2 * R + S::SA);
+                if constexpr (!S::F32) {
+                    if (i >= 2 * R) {
+                        unsigned m = 0;
+                        for (int w = 0; w < S::NT / 32; ++w) m = max(m, wmax[(i & 1) * (S::NT / 32) + w]);
+                        if (m) atomicMax(p.amax + (int64_t)slot_out * p.nz + z0 + (i - 2 * R), m);
+                    }
+                }
             }
         };
         Unroll<0, S::RING>::run(body);

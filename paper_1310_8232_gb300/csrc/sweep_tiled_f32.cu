@@ -1,0 +1,26 @@
+// Tiled sweep, FP32 storage: instantiations for every built tile.
+#include "sweep_tiled_inst.cuh"
+
+namespace stencil {
+using namespace tiled_detail;
+
+#define TILES_F32(R_, E, CALL)                                                                   \
+    STENCIL_ONE(R_, E, 32, 8, CALL) STENCIL_ONE(R_, E, 32, 16, CALL) STENCIL_ONE(R_, E, 32, 32, CALL) \
+    STENCIL_ONE(R_, E, 64, 4, CALL) STENCIL_ONE(R_, E, 64, 8, CALL) STENCIL_ONE(R_, E, 64, 16, CALL)  \
+    STENCIL_ONE(R_, E, 64, 32, CALL) STENCIL_ONE(R_, E, 128, 4, CALL) STENCIL_ONE(R_, E, 128, 8, CALL) \
+    STENCIL_ONE(R_, E, 128, 16, CALL)
+
+bool tiled_config_f32(int R, int tx, int ty, TiledInfo *info)
+{
+    STENCIL_TILE_SWITCH(float, TILES_F32, return I::shape(info), return false);
+}
+int tiled_blocks_per_sm_f32(int R, int tx, int ty)
+{
+    STENCIL_TILE_SWITCH(float, TILES_F32, return I::blocks_per_sm(), return 0);
+}
+cudaError_t launch_tiled_f32(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s)
+{
+    STENCIL_TILE_SWITCH(float, TILES_F32, return I::launch(m, p, s), return cudaErrorInvalidConfiguration);
+}
+
+}  // namespace stencil

@@ -1,0 +1,97 @@
+// Instantiation and dispatch of the tiled sweep for one storage type; each
+// sweep_tiled_*.cu includes this with its element type.
+#pragma once
+
+#include <mutex>
+
+#include "internal.h"
+#include "sweep_tiled.cuh"
+
+namespace stencil {
+namespace tiled_detail {
+
+constexpr int SMEM_LIMIT = 227 * 1024;
+
+template <int R, int TX, int TY, typename E>
+struct Inst {
+    using S = TiledShape<R, TX, TY, E>;
+    static constexpr bool fits = S::VALID && S::SMEM <= SMEM_LIMIT;
+
+    static cudaError_t prepare()
+    {
+        if constexpr (!fits) {
+            return cudaErrorInvalidConfiguration;
+        } else {
+            static std::once_flag once;
+            static cudaError_t status = cudaSuccess;
+            std::call_once(once, [] {
+                status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+            });
+            return status;
+        }
+    }
+
+    static int blocks_per_sm()
+    {
+        if constexpr (!fits) {
+            return 0;
+        } else {
+            if (prepare() != cudaSuccess) return 0;
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tiled_kernel<R, TX, TY, E>, S::NT,
+                                                              S::SMEM) != cudaSuccess)
+                return 0;
+            return n;
+        }
+    }
+
+    static bool shape(TiledInfo *info)
+    {
+        info->smem = S::SMEM;
+        info->threads = S::NT;
+        info->hx = S::HX;
+        info->zmax = S::ZMAX;
+        return fits;
+    }
+
+    static cudaError_t launch(const TiledMaps &m, const SweepParams &p, cudaStream_t s)
+    {
+        if constexpr (!fits) {
+            return cudaErrorInvalidConfiguration;
+        } else {
+            cudaError_t e = prepare();
+            if (e != cudaSuccess) return e;
+            const int tiles_x = (p.nx + TX - 1) / TX;
+            const int tiles_y = (p.ny + TY - 1) / TY;
+            const int zc = p.zchunk > 0 ? p.zchunk : p.nz;
+            if (S::ZMAX && zc > S::ZMAX) return cudaErrorInvalidValue;
+            const int nzc = (p.nz + zc - 1) / zc;
+            if ((int64_t)tiles_x * tiles_y > 0x7fffffff || nzc > 65535) return cudaErrorInvalidConfiguration;
+            SweepParams q = p;
+            q.tiles_x = tiles_x;
+            q.zchunk = zc;
+            dim3 grid(tiles_x * tiles_y, nzc);
+            sweep_tiled_kernel<R, TX, TY, E><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
+            return cudaGetLastError();
+        }
+    }
+};
+
+// Calls F<R, TX, TY>::fn(...) for the runtime (R, tx, ty); the tile list is
+// the one the library is built with for this storage type.
+#define STENCIL_TILE_SWITCH(E, TILES, CALL, MISS)                                   \
+    do {                                                                            \
+        if (R == 4) {                                                               \
+            TILES(4, E, CALL)                                                       \
+        } else if (R == 5) {                                                        \
+            TILES(5, E, CALL)                                                       \
+        }                                                                           \
+        MISS;                                                                       \
+    } while (0)
+
+#define STENCIL_ONE(R_, E, TX_, TY_, CALL) \
+    if (tx == TX_ && ty == TY_) { using I = Inst<R_, TX_, TY_, E>; CALL; }
+
+}  // namespace tiled_detail
+}  // namespace stencil

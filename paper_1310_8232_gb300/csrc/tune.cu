@@ -117,41 +117,47 @@ struct Cand {
 static const int TX_VALUES[] = {32, 64, 128};
 static const int TY_VALUES[] = {4, 8, 16, 32};
 
-static std::vector<int> zchunk_values(int nz)
+// z-chunks 8, 16, 32, ... below nz, then nz (capped for 16-bit storage)
+static std::vector<int> zchunk_values(int nz, int zmax)
 {
+    const int top = zmax > 0 ? std::min(nz, zmax) : nz;
     std::vector<int> z;
-    for (int v = 8; v < nz; v *= 2) z.push_back(v);
-    z.push_back(nz);
+    for (int v = 8; v < top; v *= 2) z.push_back(v);
+    z.push_back(top);
     return z;
 }
 
-static bool feasible(int R, int tx, int ty)
+static bool feasible(int R, int storage, int tx, int ty, int *zmax = nullptr)
 {
-    int smem, threads, hx;
-    return tiled_config(R, tx, ty, &smem, &threads, &hx);
+    TiledInfo info;
+    if (!tiled_config(R, storage, tx, ty, &info)) return false;
+    if (zmax) *zmax = info.zmax;
+    return true;
 }
 
 // Every tile the library can run for this grid, (tx, ty, zc) in that order.
-static std::vector<Cand> admissible(int R, int nz)
+static std::vector<Cand> admissible(int R, int storage, int nz)
 {
     std::vector<Cand> out;
+    int zmax = 0;
     for (int tx : TX_VALUES)
         for (int ty : TY_VALUES)
-            if (feasible(R, tx, ty))
-                for (int zc : zchunk_values(nz)) out.push_back({tx, ty, zc});
+            if (feasible(R, storage, tx, ty, &zmax))
+                for (int zc : zchunk_values(nz, zmax)) out.push_back({tx, ty, zc});
     return out;
 }
 
 // The P-part candidate set of Sec. 3.7, one axis list per tile parameter.
-static std::vector<Cand> candidate_set(int R, int nz, int P)
+static std::vector<Cand> candidate_set(int R, int storage, int nz, int P)
 {
     std::vector<int> txs(std::begin(TX_VALUES), std::end(TX_VALUES));
     std::vector<int> tys(std::begin(TY_VALUES), std::end(TY_VALUES));
     std::vector<Cand> out;
+    int zmax = 0;
     for (int tx : pick_axis(txs, P))
         for (int ty : pick_axis(tys, P))
-            if (feasible(R, tx, ty))
-                for (int zc : pick_axis(zchunk_values(nz), P)) out.push_back({tx, ty, zc});
+            if (feasible(R, storage, tx, ty, &zmax))
+                for (int zc : pick_axis(zchunk_values(nz, zmax), P)) out.push_back({tx, ty, zc});
     return out;
 }
 
@@ -167,18 +173,19 @@ struct View {
 
 static int make_view(const Plan *p, const Cand &c, int z0, int nzs, View *v)
 {
-    int smem, threads, hx;
-    if (!tiled_config(p->R, c.tx, c.ty, &smem, &threads, &hx))
+    TiledInfo info;
+    if (!tiled_config(p->R, p->storage, c.tx, c.ty, &info))
         return fail(STENCIL_EUNSUPPORTED, "tile %dx%d unavailable", c.tx, c.ty);
     v->z0 = z0;
     v->nzs = nzs;
     v->c = c;
     const int64_t off = (int64_t)z0 * p->pitch * p->ny;
     for (int par = 0; par < 2; ++par) {
-        int rc = encode_map(&v->maps[par].u_halo, p->buf[par] + off, p->nx, p->ny, nzs, p->pitch, 4,
-                            c.tx + 2 * hx, c.ty + 2 * p->R);
-        if (!rc) rc = encode_map(&v->maps[par].up_core, p->buf[par ^ 1] + off, p->nx, p->ny, nzs, p->pitch, 4, c.tx,
-                                 c.ty);
+        int rc = encode_map(&v->maps[par].u_halo, p->bptr(par, off), p->nx, p->ny, nzs, p->pitch, p->esize,
+                            c.tx + 2 * info.hx, c.ty + 2 * p->R);
+        if (!rc)
+            rc = encode_map(&v->maps[par].up_core, p->bptr(par ^ 1, off), p->nx, p->ny, nzs, p->pitch, p->esize,
+                            c.tx, c.ty);
         if (!rc) rc = encode_map(&v->maps[par].k_core, p->kappa + off, p->nx, p->ny, nzs, p->pitch, 4, c.tx, c.ty);
         if (rc) return rc;
     }
@@ -190,12 +197,12 @@ static cudaError_t sweep_view(const Plan *p, const View &v, int parity, cudaStre
     const int64_t off = (int64_t)v.z0 * p->pitch * p->ny;
     SweepParams prm = p->params(parity, 0);
     prm.nz = v.nzs;
-    prm.u = p->buf[parity] + off;
-    prm.up = p->buf[parity ^ 1] + off;
+    prm.u = p->bptr(parity, off);
+    prm.up = p->bptr(parity ^ 1, off);
     prm.kappa = p->kappa + off;
     prm.zchunk = std::min(v.c.zc, v.nzs);
     prm.src.on = 0;
-    return launch_tiled(p->R, v.c.tx, v.c.ty, v.maps[parity], prm, s);
+    return launch_tiled(p->R, p->storage, v.c.tx, v.c.ty, v.maps[parity], prm, s);
 }
 
 struct Streams {
@@ -284,8 +291,8 @@ int tune_plan(Plan *p, const stencil_desc *d)
     if (rc) return rc;
 
     std::vector<Cand> cands = (mode == STENCIL_TUNE_EXHAUSTIVE || mode == STENCIL_TUNE_OWN)
-                                  ? admissible(p->R, p->nz)
-                                  : candidate_set(p->R, p->nz, P);
+                                  ? admissible(p->R, p->storage, p->nz)
+                                  : candidate_set(p->R, p->storage, p->nz, P);
     if (cands.empty()) return fail(STENCIL_EUNSUPPORTED, "no feasible tile");
     Cand chosen{};
     double min_ms = 0, actual_ms = 0;
@@ -347,10 +354,10 @@ int tune_plan(Plan *p, const stencil_desc *d)
         if (mode == STENCIL_TUNE_EXHAUSTIVE) {
             run = cands;
         } else {
-            const int zdef = default_tile(p->R, p->nx, p->ny, p->nz).zchunk;
             for (int tx : TX_VALUES)
                 for (int ty : TY_VALUES)
-                    if (feasible(p->R, tx, ty)) run.push_back({tx, ty, zdef});
+                    if (feasible(p->R, p->storage, tx, ty))
+                        run.push_back({tx, ty, choose_zchunk(p->R, p->storage, tx, ty, p->nx, p->ny, p->nz)});
         }
         double best = 0;
         for (const Cand &c : run) {
@@ -362,7 +369,9 @@ int tune_plan(Plan *p, const stencil_desc *d)
             }
         }
         if (mode == STENCIL_TUNE_OWN) {
-            for (int zc : zchunk_values(p->nz)) {
+            int zmax = 0;
+            feasible(p->R, p->storage, chosen.tx, chosen.ty, &zmax);
+            for (int zc : zchunk_values(p->nz, zmax)) {
                 const Cand c{chosen.tx, chosen.ty, zc};
                 double ms;
                 if ((rc = time_full(p, S, c, nI, &ms))) return rc;
@@ -401,9 +410,11 @@ int tune_plan(Plan *p, const stencil_desc *d)
     p->tile.zchunk = chosen.zc;
     p->drop_graphs();
     if ((rc = p->build_maps())) return rc;
-    const size_t fbytes = (size_t)p->field_elems * sizeof(float);
+    const size_t fbytes = (size_t)p->field_elems * p->esize;
     cudaError_t e = cudaMemsetAsync(p->buf[0], 0, fbytes, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->buf[1], 0, fbytes, p->stream);
+    if (e == cudaSuccess && p->d_scale) e = cudaMemsetAsync(p->d_scale, 0, sizeof(float) * 4 * p->nz, p->stream);
+    if (e == cudaSuccess && p->d_amax) e = cudaMemsetAsync(p->d_amax, 0, sizeof(unsigned) * 4 * p->nz, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "clear after tuning");
     p->min_time_ms = min_ms;
