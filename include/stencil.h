@@ -59,6 +59,7 @@ extern "C" {
 #define STENCIL_EUNKNOWN_TICKET -8  /* no such shot ticket */
 #define STENCIL_ENODEV          -9  /* no usable CUDA device */
 #define STENCIL_EUNSUPPORTED   -10  /* configuration not built into this library */
+#define STENCIL_ECANCELLED     -11  /* the shot was cancelled (server shut down before admitting it) */
 
 /* ---- enums ----------------------------------------------------------- */
 typedef enum {
@@ -204,6 +205,95 @@ STENCIL_API int stencil_set_fields(stencil_plan_t p, const float *u, const float
 STENCIL_API int stencil_set_velocity(stencil_plan_t p, const float *velocity, int32_t on_device);
 
 STENCIL_API int stencil_get_stats(stencil_plan_t p, stencil_stats *s);
+
+/* ---- batches: many shots, one launch per time step --------------------- */
+
+/* Shots are the paper's unit of data parallelism (one grid per process,
+ * Sec. 3.1, 3.5); a batch runs many shots of different grid sizes together:
+ * every time step is one launch over all the shots' tiles, and steps are
+ * replayed from a captured CUDA graph of graph_steps steps (0 = no graph).
+ * All descriptors must share radius and storage; descs[0] gives the stream
+ * (NULL = the batch creates one) and the tile shape (tx, ty; the z-chunk is
+ * chosen for the whole batch).  Each shot keeps its own wavefields, kappa,
+ * source and step counter, and computes exactly what stencil_run computes
+ * for it alone. */
+typedef struct stencil_batch_s *stencil_batch_t;
+
+STENCIL_API int stencil_batch_create(const stencil_desc *descs, int32_t n, int32_t graph_steps,
+                                     stencil_batch_t *out);
+/* Enqueue nsteps time steps of every shot; returns without waiting. */
+STENCIL_API int stencil_batch_run(stencil_batch_t b, int32_t nsteps);
+/* Wait for the batch's stream; report device-side errors. */
+STENCIL_API int stencil_batch_sync(stencil_batch_t b);
+STENCIL_API int stencil_batch_size(stencil_batch_t b, int32_t *n);
+/* The plan of shot i, for stencil_get_field / set_fields / energy / rel_l2 /
+ * get_stats (the batch owns it: never pass it to stencil_destroy). */
+STENCIL_API int stencil_batch_plan(stencil_batch_t b, int32_t shot, stencil_plan_t *plan);
+/* The z-chunk the batch runs with. */
+STENCIL_API int stencil_batch_zchunk(stencil_batch_t b, int32_t *zchunk);
+STENCIL_API int stencil_batch_destroy(stencil_batch_t b);
+
+/* ---- shot server: continuous batching ----------------------------------- */
+
+/* A request loop for seismic shots arriving at any time.  One engine thread
+ * admits queued shots in arrival order whenever a slot is free and the
+ * shot's projected device bytes fit under the memory budget, keeps every
+ * admitted shot's wavefields resident, and advances all resident shots
+ * together, chunk_steps time steps per iteration, one launch per step over
+ * all their tiles (the batch engine).  A shot that reaches its step count
+ * retires: u^N is copied to its host buffer and its memory is freed.  Each
+ * shot's result is exactly what stencil_run computes for it alone.  All
+ * entry points are thread-safe. */
+typedef struct shot_server_s *shot_server_t;
+
+typedef struct {
+    double  hbm_budget_frac;    /* share of the device's total memory the server may hold (default 0.8) */
+    int64_t hbm_budget_bytes;   /* > 0: a byte budget instead of the fraction */
+    int32_t max_slots;          /* resident shots at most (default 64) */
+    int32_t chunk_steps;        /* time steps per engine iteration (default 20) */
+    int32_t radius;             /* every shot's radius (default 5) */
+    int32_t storage;            /* every shot's storage (default FP32) */
+    void   *cuda_stream;        /* NULL = the server creates one */
+    stencil_tile tile;          /* tile shape (AUTO = 64 x 16) */
+} shot_server_cfg;
+
+typedef enum { SHOT_QUEUED = 0, SHOT_RUNNING = 1, SHOT_DONE = 2, SHOT_FAILED = 3 } shot_state;
+
+typedef struct {
+    double  t_submit, t_admit, t_done;  /* seconds since the server was created; < 0 = not yet */
+    int64_t steps_done;
+    int32_t status;                     /* STENCIL_OK, or why the shot failed */
+    int32_t pad;
+} shot_timing;
+
+typedef struct {
+    int64_t submitted, admitted, done, failed, queued, running;
+    int64_t bytes_in_use, budget_bytes;
+    int64_t iterations;                 /* engine iterations run */
+    int64_t point_updates;              /* nx*ny*nz*steps summed over finished shots */
+    double  busy_s;                     /* engine time spent stepping resident shots */
+    double  admit_s;                    /* engine time spent admitting shots (plan set-up) */
+    double  build_s;                    /* engine time spent re-describing the resident set */
+    double  retire_s;                   /* retire-thread time (read-back and free) */
+} shot_server_stats;
+
+STENCIL_API void shot_server_cfg_init(shot_server_cfg *cfg);
+STENCIL_API int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out);
+/* Queue a shot of nsteps time steps; u^N will be written to out_host (dense
+ * nx*ny*nz floats, or NULL), which must stay valid until the shot is DONE or
+ * FAILED.  A host velocity is copied at once; a device velocity must stay
+ * valid until the shot is admitted.  STENCIL_EBUDGET if the shot alone
+ * exceeds the budget (it is recorded as FAILED). */
+STENCIL_API int shot_submit(shot_server_t s, const stencil_desc *d, int32_t nsteps, float *out_host,
+                            uint64_t *ticket);
+/* State (shot_state) and timing of a shot; does not block. */
+STENCIL_API int shot_poll(shot_server_t s, uint64_t ticket, int32_t *state, shot_timing *t);
+/* Block until the shot is DONE or FAILED, or timeout_s passes (STENCIL_ENOTREADY). */
+STENCIL_API int shot_wait(shot_server_t s, uint64_t ticket, double timeout_s, int32_t *state);
+STENCIL_API int shot_server_get_stats(shot_server_t s, shot_server_stats *out);
+/* Finish the resident shots, cancel the queued ones (FAILED,
+ * STENCIL_ECANCELLED), stop the engine and free everything. */
+STENCIL_API int shot_server_destroy(shot_server_t s);
 
 /* ---- FP64 validation reductions (on the device, deterministic) -------- */
 

@@ -36,6 +36,8 @@ STENCIL_ENOTREADY = -7
 STENCIL_EUNKNOWN_TICKET = -8
 STENCIL_ENODEV = -9
 STENCIL_EUNSUPPORTED = -10
+STENCIL_ECANCELLED = -11
+SHOT_QUEUED, SHOT_RUNNING, SHOT_DONE, SHOT_FAILED = 0, 1, 2, 3
 
 STENCIL_FP32, STENCIL_FP16, STENCIL_BF16 = 0, 1, 2
 STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_TILED = 0, 1, 2
@@ -88,6 +90,30 @@ class stencil_stats(ctypes.Structure):
     ]
 
 
+class shot_server_cfg(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_frac", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_int64),
+        ("max_slots", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
+        ("radius", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("cuda_stream", ctypes.c_void_p), ("tile", stencil_tile),
+    ]
+
+
+class shot_timing(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("steps_done", ctypes.c_int64), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class shot_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("done", ctypes.c_int64),
+        ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+        ("bytes_in_use", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+        ("iterations", ctypes.c_int64), ("point_updates", ctypes.c_int64), ("busy_s", ctypes.c_double),
+        ("admit_s", ctypes.c_double), ("build_s", ctypes.c_double), ("retire_s", ctypes.c_double),
+    ]
+
+
 # ---- prototypes ----------------------------------------------------------------
 _P = ctypes.c_void_p
 _I = ctypes.c_int32
@@ -109,6 +135,21 @@ _lib.stencil_select.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, _I, _I,
                                 ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_select_ob.argtypes = [ctypes.POINTER(ctypes.c_double), _I, _I, ctypes.POINTER(_I),
                                    ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]
+_lib.stencil_batch_create.argtypes = [ctypes.POINTER(stencil_desc), _I, _I, ctypes.POINTER(_P)]
+_lib.stencil_batch_run.argtypes = [_P, _I]
+_lib.stencil_batch_sync.argtypes = [_P]
+_lib.stencil_batch_size.argtypes = [_P, ctypes.POINTER(_I)]
+_lib.stencil_batch_plan.argtypes = [_P, _I, ctypes.POINTER(_P)]
+_lib.stencil_batch_zchunk.argtypes = [_P, ctypes.POINTER(_I)]
+_lib.stencil_batch_destroy.argtypes = [_P]
+_lib.shot_server_cfg_init.argtypes = [ctypes.POINTER(shot_server_cfg)]
+_lib.shot_server_cfg_init.restype = None
+_lib.shot_server_create.argtypes = [ctypes.POINTER(shot_server_cfg), ctypes.POINTER(_P)]
+_lib.shot_submit.argtypes = [_P, ctypes.POINTER(stencil_desc), _I, _P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.shot_poll.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(shot_timing)]
+_lib.shot_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_I)]
+_lib.shot_server_get_stats.argtypes = [_P, ctypes.POINTER(shot_server_stats)]
+_lib.shot_server_destroy.argtypes = [_P]
 _lib.stencil_sqdiff_noalloc.argtypes = [_P, ctypes.c_int64, _P, _I, _I, _I, _P, _P]
 _lib.stencil_tile_info.argtypes = [_I, _I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]
 _lib.stencil_tile_info.restype = ctypes.c_int
@@ -119,7 +160,10 @@ _lib.stencil_version.restype = ctypes.c_char_p
 for _name in ("stencil_plan", "stencil_destroy", "stencil_step", "stencil_run", "stencil_sync",
               "stencil_get_field", "stencil_set_fields", "stencil_get_stats", "stencil_energy",
               "stencil_rel_l2", "stencil_set_velocity", "stencil_candidates_1d", "stencil_select",
-              "stencil_select_ob", "stencil_sqdiff_noalloc"):
+              "stencil_select_ob", "stencil_sqdiff_noalloc", "stencil_batch_create", "stencil_batch_run",
+              "stencil_batch_sync", "stencil_batch_size", "stencil_batch_plan", "stencil_batch_zchunk",
+              "stencil_batch_destroy", "shot_server_create", "shot_submit", "shot_poll", "shot_wait",
+              "shot_server_get_stats", "shot_server_destroy"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -270,6 +314,90 @@ def stencil_tile_info(radius: int, tx: int, ty: int, storage: int = STENCIL_FP32
     return None
 
 
+def stencil_batch_create(descs, graph_steps: int = 0) -> int:
+    """Batch of shots from a list of stencil_desc (their velocity arrays must
+    stay alive until this returns).  Returns the batch handle."""
+    arr = (stencil_desc * len(descs))(*descs)
+    h = _P()
+    _check(_lib.stencil_batch_create(arr, len(descs), graph_steps, ctypes.byref(h)))
+    return h.value
+
+
+def stencil_batch_run(batch: int, nsteps: int) -> None:
+    _check(_lib.stencil_batch_run(batch, nsteps))
+
+
+def stencil_batch_sync(batch: int) -> None:
+    _check(_lib.stencil_batch_sync(batch))
+
+
+def stencil_batch_size(batch: int) -> int:
+    n = _I()
+    _check(_lib.stencil_batch_size(batch, ctypes.byref(n)))
+    return n.value
+
+
+def stencil_batch_plan(batch: int, shot: int) -> int:
+    h = _P()
+    _check(_lib.stencil_batch_plan(batch, shot, ctypes.byref(h)))
+    return h.value
+
+
+def stencil_batch_zchunk(batch: int) -> int:
+    z = _I()
+    _check(_lib.stencil_batch_zchunk(batch, ctypes.byref(z)))
+    return z.value
+
+
+def stencil_batch_destroy(batch: int) -> None:
+    _check(_lib.stencil_batch_destroy(batch))
+
+
+def shot_server_cfg_init() -> shot_server_cfg:
+    c = shot_server_cfg()
+    _lib.shot_server_cfg_init(ctypes.byref(c))
+    return c
+
+
+def shot_server_create(cfg: shot_server_cfg) -> int:
+    h = _P()
+    _check(_lib.shot_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def shot_submit(server: int, desc: stencil_desc, nsteps: int, out_host=None) -> int:
+    """Queue a shot; out_host (numpy float32, nz x ny x nx) must stay alive until it finishes."""
+    t = ctypes.c_uint64()
+    addr, dev = _ptr(out_host)
+    if dev:
+        raise ValueError("out_host must be host memory")
+    _check(_lib.shot_submit(server, ctypes.byref(desc), nsteps, addr or None, ctypes.byref(t)))
+    return t.value
+
+
+def shot_poll(server: int, ticket: int) -> tuple[int, shot_timing]:
+    st_ = _I()
+    tm = shot_timing()
+    _check(_lib.shot_poll(server, ticket, ctypes.byref(st_), ctypes.byref(tm)))
+    return st_.value, tm
+
+
+def shot_wait(server: int, ticket: int, timeout_s: float = 60.0) -> int:
+    st_ = _I()
+    _check(_lib.shot_wait(server, ticket, timeout_s, ctypes.byref(st_)))
+    return st_.value
+
+
+def shot_server_get_stats(server: int) -> shot_server_stats:
+    s_ = shot_server_stats()
+    _check(_lib.shot_server_get_stats(server, ctypes.byref(s_)))
+    return s_
+
+
+def shot_server_destroy(server: int) -> None:
+    _check(_lib.shot_server_destroy(server))
+
+
 def stencil_cfl_limit(radius: int) -> float:
     return float(_lib.stencil_cfl_limit(radius))
 
@@ -315,6 +443,9 @@ EXPORTED = [
     "stencil_get_stats",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
-    "stencil_tile_info",
+    "stencil_tile_info", "stencil_batch_create", "stencil_batch_run", "stencil_batch_sync",
+    "stencil_batch_size", "stencil_batch_plan", "stencil_batch_zchunk", "stencil_batch_destroy",
+    "shot_server_cfg_init", "shot_server_create", "shot_submit", "shot_poll", "shot_wait",
+    "shot_server_get_stats", "shot_server_destroy",
     "stencil_version",
 ]

@@ -82,6 +82,22 @@ struct SweepParams {
     int *err;                      // device error word
 };
 
+// A shot of a grouped launch: its tensor maps (by parity of the level),
+// buffers and parameters, in 64-byte aligned device memory.
+struct alignas(64) GroupShot {
+    CUtensorMap halo[2];           // u^n halo boxes, by which buffer holds u^n
+    CUtensorMap core[2];           // u^{n-1} core boxes, by buffer
+    CUtensorMap kcore;             // kappa
+    SweepParams prm;               // u, up are set per step from buf[]
+    void *buf[2];
+    int64_t n_end;                 // step counter value at which the shot stops
+    int32_t parity_base;           // buffer of u^n = (n + parity_base) & 1
+    int32_t pad;
+};
+struct GroupItem {
+    int32_t shot, bx, by, z0, z1;
+};
+
 __device__ __forceinline__ int64_t current_step(const SweepParams &p)
 {
     return *p.step_base + p.step_off;
@@ -165,6 +181,14 @@ __device__ __forceinline__ void tma_load_3d_hint(void *dst, const CUtensorMap *m
         " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z), "l"(policy)
         : "memory");
+}
+
+// Make a tensor map that was (re)written in global memory visible to this
+// thread's TMA copies.
+__device__ __forceinline__ void fence_tensormap(const CUtensorMap *map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
 }
 
 __device__ __forceinline__ uint64_t policy_evict_first()

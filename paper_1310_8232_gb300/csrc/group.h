@@ -1,0 +1,36 @@
+// Grouped execution of many plans (shots) in one launch per time step: the
+// engine behind stencil_batch_* and the shot server.
+#pragma once
+
+#include <vector>
+
+#include "plan_impl.h"
+
+namespace stencil {
+
+struct Group {
+    int R = 5, storage = 0, tx = 64, ty = 16, zchunk = 32;
+    cudaStream_t stream = nullptr;
+    GroupShot *d_shots = nullptr;
+    GroupItem *d_items = nullptr;
+    int cap_shots = 0, cap_items = 0;
+    int n_shots = 0, n_items = 0;
+    std::vector<GroupShot> h_shots;
+    std::vector<GroupItem> h_items;
+    int graph_len = 0;
+    cudaGraphExec_t graph = nullptr;
+
+    ~Group() { release(); }
+    void release();
+    // Describe `plans` (same radius, storage and tile shape) to the device;
+    // shot i stops when its counter reaches n_end[i].  Enqueued on stream.
+    int build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n_end);
+    // Enqueue k steps of every shot (k grouped launches + one counter advance),
+    // through a captured graph of graph_len steps where k allows.
+    int step(int k);
+};
+
+// A common z-chunk for the blocks of several grids sharing the GPU.
+int group_zchunk(int R, int storage, int tx, int ty, const std::vector<Plan *> &plans);
+
+}  // namespace stencil

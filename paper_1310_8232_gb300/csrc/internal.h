@@ -60,6 +60,19 @@ cudaError_t launch_tiled_f32(int R, int tx, int ty, const TiledMaps &m, const Sw
 cudaError_t launch_tiled_f16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
 cudaError_t launch_tiled_bf16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
 
+// grouped launch: one time step of every shot in `shots` (device array),
+// n_items blocks, block b doing items[b]
+cudaError_t launch_grouped(int R, int storage, int tx, int ty, const GroupShot *shots, const GroupItem *items,
+                           int n_items, int step_off, cudaStream_t s);
+cudaError_t launch_grouped_f32(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
+                               int step_off, cudaStream_t s);
+cudaError_t launch_grouped_f16(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
+                               int step_off, cudaStream_t s);
+cudaError_t launch_grouped_bf16(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
+                                int step_off, cudaStream_t s);
+// n[i] = min(n[i] + k, n_end[i]) for the shots of a group
+cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStream_t s);
+
 // ---- K2 helpers: 16-bit fields <-> FP32 with per-plane power-of-two scales ----
 // pack: src FP32 (pitch elements) -> dst 16-bit; writes amax[z] (max |src|
 // over plane z, float bits) and scale[z] (the power of two used).

@@ -226,6 +226,23 @@ cudaError_t launch_sqdiff(const float *a, const double *b, int nx, int ny, int n
 
 __global__ void advance_kernel(int64_t *n, int k) { *n += k; }
 
+// each shot's counter moves k steps, but never past its last step
+__global__ void group_advance_kernel(GroupShot *shots, int n_shots, int k)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_shots; i += gridDim.x * blockDim.x) {
+        int64_t *n = const_cast<int64_t *>(shots[i].prm.step_base);
+        const int64_t v = *n + k;
+        *n = v < shots[i].n_end ? v : shots[i].n_end;
+    }
+}
+
+cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStream_t s)
+{
+    if (n_shots <= 0) return cudaSuccess;
+    group_advance_kernel<<<(n_shots + 127) / 128, 128, 0, s>>>(shots, n_shots, k);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s)
 {
     advance_kernel<<<1, 1, 0, s>>>(n, k);

@@ -81,6 +81,15 @@ int tiled_blocks_per_sm(int R, int storage, int tx, int ty)
     return 0;
 }
 
+cudaError_t launch_grouped(int R, int storage, int tx, int ty, const GroupShot *shots, const GroupItem *items,
+                           int n_items, int step_off, cudaStream_t s)
+{
+    if (storage == STENCIL_FP32) return launch_grouped_f32(R, tx, ty, shots, items, n_items, step_off, s);
+    if (storage == STENCIL_FP16) return launch_grouped_f16(R, tx, ty, shots, items, n_items, step_off, s);
+    if (storage == STENCIL_BF16) return launch_grouped_bf16(R, tx, ty, shots, items, n_items, step_off, s);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_tiled(int R, int storage, int tx, int ty, const TiledMaps &m, const SweepParams &p,
                          cudaStream_t s)
 {
@@ -121,6 +130,32 @@ int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(STENCIL_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return STENCIL_OK;
+}
+
+// Small device-to-host reads go through a pinned per-thread buffer: a copy
+// into pageable memory waits for any other thread's pageable copy in
+// flight (the driver stages them), which would stall e.g. plan set-up
+// behind a large read-back on another thread.
+static void *pinned_scratch()
+{
+    thread_local void *buf = nullptr;
+    if (!buf && cudaMallocHost(&buf, 256) != cudaSuccess) buf = nullptr;
+    return buf;
+}
+
+// Read `bytes` (<= 256) of device memory into host `dst` through the pinned
+// scratch; synchronises `s`.
+static cudaError_t read_small(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    void *pin = pinned_scratch();
+    if (!pin) {
+        cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+        return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+    }
+    cudaError_t e = cudaMemcpyAsync(pin, src, bytes, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) std::memcpy(dst, pin, bytes);
+    return e;
 }
 
 // ---- plan internals -----------------------------------------------------------
@@ -253,8 +288,7 @@ int Plan::enqueue(int nsteps)
 int Plan::check_device_error()
 {
     int h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaError_t e = read_small(&h, d_err, sizeof(int), stream);
     if (e != cudaSuccess) return fail_cuda(e, "stream synchronize");
     if (h) {
         cudaMemsetAsync(d_err, 0, sizeof(int), stream);
@@ -270,12 +304,13 @@ void Plan::release()
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
     for (auto &b : buf)
-        if (b) cudaFree(b);
+        if (b) dev_free(b);
     for (auto &b : staging)
-        if (b) cudaFree(b);
+        if (b) dev_free(b);
     staging[0] = staging[1] = nullptr;
-    if (kappa) cudaFree(kappa);
-    if (d_scratch) cudaFree(d_scratch);
+    if (kappa) dev_free(kappa);
+    if (d_scratch) dev_free(d_scratch);
+    if (pool && stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
     buf[0] = buf[1] = nullptr;
     kappa = nullptr;
@@ -300,10 +335,12 @@ int Plan::load_velocity(const float *v, int on_device)
     if (e != cudaSuccess) return fail_cuda(e, "coef_init");
     unsigned vmax_bits = 0;
     unsigned long long nbad = 0;
-    cudaMemcpyAsync(&vmax_bits, d_vmax, sizeof vmax_bits, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&nbad, d_bad, sizeof nbad, cudaMemcpyDeviceToHost, s);
-    e = cudaStreamSynchronize(s);
+    // d_vmax and d_bad are adjacent in the scratch block (offsets 16 and 24)
+    unsigned char both[16];
+    e = read_small(both, d_vmax, sizeof both, s);
     if (e != cudaSuccess) return fail_cuda(e, "velocity setup");
+    std::memcpy(&vmax_bits, both, sizeof vmax_bits);
+    std::memcpy(&nbad, both + 8, sizeof nbad);
     velocity_ok = false;
     if (nbad) return fail(STENCIL_EINVAL, "%llu velocities are not finite and > 0", nbad);
     float vm;
@@ -321,11 +358,23 @@ int Plan::load_velocity(const float *v, int on_device)
     return STENCIL_OK;
 }
 
+cudaError_t Plan::dev_alloc(void **ptr, size_t bytes)
+{
+    if (pool) return cudaMallocFromPoolAsync(ptr, bytes, pool, stream);
+    return cudaMalloc(ptr, bytes);
+}
+
+void Plan::dev_free(void *ptr)
+{
+    if (pool) cudaFreeAsync(ptr, stream);
+    else cudaFree(ptr);
+}
+
 int Plan::ensure_staging()
 {
     for (auto &b : staging)
         if (!b) {
-            cudaError_t e = cudaMalloc(&b, (size_t)field_elems * sizeof(float));
+            cudaError_t e = dev_alloc(reinterpret_cast<void **>(&b), (size_t)field_elems * sizeof(float));
             if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc(staging)");
             e = cudaMemsetAsync(b, 0, (size_t)field_elems * sizeof(float), stream);
             if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync(staging)");
@@ -453,7 +502,7 @@ int check_tile(int R, int storage, const stencil_tile &t)
     return STENCIL_OK;
 }
 
-int plan_create(const stencil_desc *d, Plan **out)
+int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
 {
     int rc = validate_desc(d);
     if (rc) return rc;
@@ -465,6 +514,7 @@ int plan_create(const stencil_desc *d, Plan **out)
     }
     Plan *p = new Plan();
     p->dev = dev;
+    p->pool = pool;
     p->R = d->radius;
     p->nx = d->nx;
     p->ny = d->ny;
@@ -492,17 +542,17 @@ int plan_create(const stencil_desc *d, Plan **out)
     const size_t fbytes = (size_t)p->field_elems * p->esize;
     const size_t kbytes = (size_t)p->field_elems * sizeof(float);
     for (auto &b : p->buf) {
-        e = cudaMalloc(&b, fbytes);
+        e = p->dev_alloc(&b, fbytes);
         if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(field)"));
     }
-    e = cudaMalloc(&p->kappa, kbytes);
+    e = p->dev_alloc(reinterpret_cast<void **>(&p->kappa), kbytes);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(kappa)"));
     // scratch: step counter, error word, v range, reduction partials and
     // result, and (16-bit storage) the per-level per-plane scale and amax tables
     const size_t red_bytes = 256 + sizeof(double) * (2 * RED_BLOCKS + 8);
     const size_t tab_bytes = p->storage == STENCIL_FP32 ? 0 : (size_t)8 * 4 * d->nz;
     const size_t scratch = red_bytes + tab_bytes;
-    e = cudaMalloc(&p->d_scratch, scratch);
+    e = p->dev_alloc(&p->d_scratch, scratch);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(scratch)"));
     unsigned char *sc = static_cast<unsigned char *>(p->d_scratch);
     p->d_step = reinterpret_cast<int64_t *>(sc);
@@ -526,8 +576,8 @@ int plan_create(const stencil_desc *d, Plan **out)
     float v_src = 0.0f;
     if (d->src_amp != 0.0) {
         const float *vs = d->velocity + ((int64_t)d->src_z * d->ny + d->src_y) * d->nx + d->src_x;
-        e = cudaMemcpyAsync(&v_src, vs, sizeof(float),
-                            d->velocity_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s);
+        if (d->velocity_on_device) e = read_small(&v_src, vs, sizeof(float), s);
+        else v_src = *vs;
         if (e != cudaSuccess) return bail(fail_cuda(e, "source velocity read"));
     }
     p->src_amp = d->src_amp;
@@ -717,8 +767,9 @@ int stencil_set_velocity(stencil_plan_t h, const float *velocity, int32_t on_dev
     float v_src = 0.0f;
     if (p->src.on) {
         const float *vs = velocity + ((int64_t)p->src.z * p->ny + p->src.y) * p->nx + p->src.x;
-        cudaError_t e = cudaMemcpyAsync(&v_src, vs, sizeof(float),
-                                        on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, p->stream);
+        cudaError_t e = cudaSuccess;
+        if (on_device) e = read_small(&v_src, vs, sizeof(float), p->stream);
+        else v_src = *vs;
         if (e != cudaSuccess) return fail_cuda(e, "source velocity read");
     }
     int rc = p->load_velocity(velocity, on_device);
@@ -764,7 +815,7 @@ int stencil_energy(stencil_plan_t h, double *out)
     cudaError_t e = launch_energy(p->R, u1, u0, p->kappa, p->nx, p->ny, p->nz, p->pitch, p->d_partials,
                                   p->d_result, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "energy");
-    e = cudaMemcpyAsync(out, p->d_result, sizeof(double), cudaMemcpyDeviceToHost, p->stream);
+    e = read_small(out, p->d_result, sizeof(double), p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "energy copy");
     return p->check_device_error();
 }
@@ -780,7 +831,7 @@ int stencil_rel_l2(stencil_plan_t h, const double *ref, double *out)
     cudaError_t e = launch_sqdiff(u1, ref, p->nx, p->ny, p->nz, p->pitch, p->d_partials, p->d_result, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "rel_l2");
     double h2[2];
-    e = cudaMemcpyAsync(h2, p->d_result, sizeof h2, cudaMemcpyDeviceToHost, p->stream);
+    e = read_small(h2, p->d_result, sizeof h2, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "rel_l2 copy");
     int rc = p->check_device_error();
     if (rc) return rc;

@@ -21,6 +21,7 @@ extern thread_local std::string g_last_error;
 
 struct Plan {
     int dev = 0;
+    cudaMemPool_t pool = nullptr;         // set: stream-ordered allocations from this pool
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int R = 5;
@@ -61,6 +62,8 @@ struct Plan {
     double min_time_ms = NAN, actual_time_ms = NAN, full_time_ms = NAN, quality = NAN, selection_ms = NAN;
     int n_candidates = 0;
 
+    cudaError_t dev_alloc(void **ptr, size_t bytes);
+    void dev_free(void *ptr);
     char *bptr(int b, int64_t off_elems) const { return static_cast<char *>(buf[b]) + off_elems * esize; }
     int ensure_staging();
     // FP32 view of level n - which (the field itself for FP32 storage, an
@@ -77,6 +80,10 @@ struct Plan {
     int check_device_error();
     void release();
 };
+
+// Build a plan; with a pool, every device allocation of the plan is
+// stream-ordered from it (no device-wide synchronisation on free).
+int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool = nullptr);
 
 // Tile selection (Sec. 3.2-3.3 on GPU tile parameters); sets p->tile.
 int tune_plan(Plan *p, const stencil_desc *d);

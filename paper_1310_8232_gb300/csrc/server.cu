@@ -1,0 +1,524 @@
+// Shot server: continuous batching of independent shots on one GPU.
+//
+// Requests (a problem description, a step count and a host output buffer)
+// arrive at any time through shot_submit.  One engine thread admits queued
+// shots in arrival order while a slot is free and the projected device bytes
+// fit under the memory budget, keeps every admitted shot's wavefields
+// resident, and advances all resident shots together, chunk_steps time steps
+// per iteration, with the grouped kernel (one launch per step over all
+// shots' tiles).  Shots that reach their step count retire: the final field
+// is copied to the caller's buffer and the shot's memory is freed by a
+// second thread on its own stream (so the engine keeps stepping the other
+// shots meanwhile), and the slot goes to the next request.  Device memory
+// comes from a server-owned stream-ordered pool, so neither admission nor
+// retirement synchronises the whole device.  shot_poll reports state and
+// timing without blocking.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "group.h"
+
+namespace stencil {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    stencil_desc desc{};
+    std::vector<float> velocity;      // host copy (desc.velocity points here unless on device)
+    int32_t nsteps = 0;
+    float *out_host = nullptr;
+    int state = SHOT_QUEUED;
+    int status = STENCIL_OK;
+    double t_submit = -1, t_admit = -1, t_done = -1;
+    int64_t steps_done = 0;
+    int64_t bytes = 0;
+    Plan *plan = nullptr;
+};
+
+int64_t projected_bytes(const stencil_desc &d)
+{
+    const int esize = d.storage == STENCIL_FP32 ? 4 : 2;
+    const int64_t elems = row_pitch(d.nx, esize) * d.ny * d.nz;
+    int64_t b = elems * (2 * esize + 4) + 64 * 1024 + 32LL * d.nz;
+    if (d.storage != STENCIL_FP32) b += 2 * elems * 4;      // FP32 staging for the final read-back
+    return b;
+}
+
+}  // namespace
+
+struct Server {
+    shot_server_cfg cfg{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t retire_stream = nullptr;
+    cudaMemPool_t pool = nullptr;
+    int64_t budget = 0;
+    Clock::time_point t0;
+
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request *> queue;
+    std::map<uint64_t, std::unique_ptr<Request>> all;
+    uint64_t next_ticket = 1;
+    bool stopping = false;
+    shot_server_stats stats{};
+
+    std::vector<Request *> resident;      // engine thread only
+    Group group;
+    std::thread engine;
+    int engine_error = STENCIL_OK;
+
+    // retirement: read-back and free on the retire thread
+    std::deque<std::pair<Request *, int>> retire_q;
+    bool retire_stop = false;
+    std::thread retirer;
+    static constexpr size_t BOUNCE_BYTES = 32u << 20;
+    float *bounce[2] = {nullptr, nullptr};    // pinned host halves for read-back
+    cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
+    int read_back(Plan *p, float *out);
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+    void run();
+    void retire_loop();
+    void retire(Request *r, int status);      // hand a shot to the retire thread
+    void finish(Request *r, int status);      // retire thread: read back, free, report
+};
+
+void Server::retire(Request *r, int status)
+{
+    std::lock_guard<std::mutex> lock(mu);
+    retire_q.emplace_back(r, status);
+    cv.notify_all();
+}
+
+void Server::retire_loop()
+{
+    cudaSetDevice(dev);
+    for (;;) {
+        std::pair<Request *, int> job;
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            cv.wait(lock, [&] { return retire_stop || !retire_q.empty(); });
+            if (retire_q.empty()) return;       // stop requested and nothing left
+            job = retire_q.front();
+            retire_q.pop_front();
+        }
+        finish(job.first, job.second);
+    }
+}
+
+// u^N of a finished shot into the caller's dense buffer, through the pinned
+// bounce halves (device-to-pinned copy of chunk k overlaps the host copy of
+// chunk k-1), so the read-back never takes the driver's pageable path.
+int Server::read_back(Plan *p, float *out)
+{
+    const float *src = nullptr;
+    int rc = p->fp32_level(0, &src);
+    if (rc) return rc;
+    const size_t row_bytes = (size_t)p->nx * sizeof(float);
+    const int64_t rows = (int64_t)p->ny * p->nz;
+    const int64_t per = std::max<int64_t>(1, (int64_t)(BOUNCE_BYTES / row_bytes));
+    int64_t prev_r0 = -1, prev_n = 0;
+    int k = 0;
+    for (int64_t r0 = 0; r0 < rows; r0 += per, ++k) {
+        const int64_t n = std::min(per, rows - r0);
+        cudaError_t e = cudaMemcpy2DAsync(bounce[k & 1], row_bytes, src + r0 * p->pitch, p->pitch * sizeof(float),
+                                          row_bytes, (size_t)n, cudaMemcpyDeviceToHost, retire_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(bounce_ev[k & 1], retire_stream);
+        if (e != cudaSuccess) return fail_cuda(e, "read-back");
+        if (prev_r0 >= 0) {
+            if ((e = cudaEventSynchronize(bounce_ev[(k - 1) & 1])) != cudaSuccess) return fail_cuda(e, "read-back");
+            std::memcpy(out + prev_r0 * p->nx, bounce[(k - 1) & 1], (size_t)prev_n * row_bytes);
+        }
+        prev_r0 = r0;
+        prev_n = n;
+    }
+    if (prev_r0 >= 0) {
+        cudaError_t e = cudaEventSynchronize(bounce_ev[(k - 1) & 1]);
+        if (e != cudaSuccess) return fail_cuda(e, "read-back");
+        std::memcpy(out + prev_r0 * p->nx, bounce[(k - 1) & 1], (size_t)prev_n * row_bytes);
+    }
+    return STENCIL_OK;
+}
+
+void Server::finish(Request *r, int status)
+{
+    const auto f0 = Clock::now();
+    int rc = status;
+    if (r->plan) {
+        // the engine has synchronised its stream after the shot's last step;
+        // from here on the shot's plan works on the retire stream
+        r->plan->stream = retire_stream;
+        r->plan->own_stream = false;
+        if (rc == STENCIL_OK && r->out_host) rc = read_back(r->plan, r->out_host);
+        r->plan->release();
+        delete r->plan;
+        r->plan = nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    stats.retire_s += std::chrono::duration<double>(Clock::now() - f0).count();
+    r->state = rc == STENCIL_OK ? SHOT_DONE : SHOT_FAILED;
+    r->status = rc;
+    r->t_done = now();
+    stats.bytes_in_use -= r->bytes;
+    stats.running -= 1;
+    if (rc == STENCIL_OK) {
+        stats.done += 1;
+        stats.point_updates += (int64_t)r->desc.nx * r->desc.ny * r->desc.nz * r->nsteps;
+    } else {
+        stats.failed += 1;
+    }
+    cv.notify_all();
+}
+
+void Server::run()
+{
+    cudaSetDevice(dev);
+    bool rebuild = false;
+    for (;;) {
+        // ---- admission -------------------------------------------------
+        std::vector<Request *> admit;
+        {
+            std::unique_lock<std::mutex> lock(mu);
+            if (resident.empty())
+                cv.wait_for(lock, std::chrono::milliseconds(20), [&] { return stopping || !queue.empty(); });
+            if (stopping) {
+                for (Request *r : queue) {
+                    r->state = SHOT_FAILED;
+                    r->status = STENCIL_ECANCELLED;
+                    r->t_done = now();
+                    stats.queued -= 1;
+                    stats.failed += 1;
+                }
+                queue.clear();
+                if (resident.empty()) {
+                    cv.notify_all();
+                    return;
+                }
+            }
+            while (!queue.empty() && (int)(resident.size() + admit.size()) < cfg.max_slots &&
+                   stats.bytes_in_use + queue.front()->bytes <= budget) {
+                Request *r = queue.front();
+                queue.pop_front();
+                stats.bytes_in_use += r->bytes;
+                stats.queued -= 1;
+                stats.running += 1;
+                r->state = SHOT_RUNNING;
+                admit.push_back(r);
+            }
+        }
+        for (Request *r : admit) {
+            const auto a0 = Clock::now();
+            stencil_desc d = r->desc;
+            d.cuda_stream = stream;
+            d.tune_mode = STENCIL_TUNE_NONE;
+            d.graph_steps = 0;
+            d.storage = cfg.storage;
+            d.radius = cfg.radius;
+            d.tile = group.tx ? stencil_tile{STENCIL_KERNEL_TILED, group.tx, group.ty, -1} : d.tile;
+            Plan *p = nullptr;
+            int rc = plan_create(&d, &p, pool);
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                r->t_admit = now();
+                stats.admitted += 1;
+                stats.admit_s += std::chrono::duration<double>(Clock::now() - a0).count();
+            }
+            if (rc) {
+                retire(r, rc);
+                continue;
+            }
+            r->plan = p;
+            r->velocity.clear();
+            r->velocity.shrink_to_fit();
+            resident.push_back(r);
+            rebuild = true;
+        }
+        if (resident.empty()) continue;
+
+        // ---- one engine iteration over every resident shot ---------------
+        auto it0 = Clock::now();
+        if (rebuild) {
+            std::vector<Plan *> plans;
+            std::vector<int64_t> n_end;
+            for (Request *r : resident) {
+                plans.push_back(r->plan);
+                n_end.push_back(r->nsteps);
+            }
+            group.zchunk = group_zchunk(group.R, group.storage, group.tx, group.ty, plans);
+            TiledInfo info{};
+            tiled_config(group.R, group.storage, group.tx, group.ty, &info);
+            if (info.zmax) group.zchunk = std::min(group.zchunk, info.zmax);
+            int rc = group.build(plans, n_end);
+            if (rc) {
+                engine_error = rc;
+                for (Request *r : resident) retire(r, rc);
+                resident.clear();
+                continue;
+            }
+            rebuild = false;
+            const auto b1 = Clock::now();
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                stats.build_s += std::chrono::duration<double>(b1 - it0).count();
+            }
+            it0 = b1;
+        }
+        int rc = group.step(cfg.chunk_steps);
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "engine iteration");
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            stats.iterations += 1;
+            stats.busy_s += std::chrono::duration<double>(Clock::now() - it0).count();
+        }
+        std::vector<Request *> keep;
+        for (size_t i = 0; i < resident.size(); ++i) {
+            Request *r = resident[i];
+            Plan *p = r->plan;
+            const int pb = group.h_shots[i].parity_base;
+            p->steps_done = std::min<int64_t>(p->steps_done + cfg.chunk_steps, r->nsteps);
+            p->cur = (int)((p->steps_done + pb) & 1);
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                r->steps_done = p->steps_done;
+            }
+            if (rc != STENCIL_OK) {
+                retire(r, rc);
+                rebuild = true;
+            } else if (p->steps_done >= r->nsteps) {
+                int drc = p->check_device_error();
+                retire(r, drc);
+                rebuild = true;
+            } else {
+                keep.push_back(r);
+            }
+        }
+        resident.swap(keep);
+    }
+}
+
+}  // namespace stencil
+
+using namespace stencil;
+
+extern "C" {
+
+void shot_server_cfg_init(shot_server_cfg *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->hbm_budget_frac = 0.8;
+    c->max_slots = 64;
+    c->chunk_steps = 20;
+    c->radius = 5;
+    c->storage = STENCIL_FP32;
+    c->tile.kernel = STENCIL_KERNEL_AUTO;
+}
+
+int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
+{
+    if (!cfg || !out) return fail(STENCIL_EINVAL, "null argument");
+    *out = nullptr;
+    if (cfg->radius != 4 && cfg->radius != 5) return fail(STENCIL_EINVAL, "radius must be 4 or 5");
+    if (cfg->max_slots < 1 || cfg->chunk_steps < 1) return fail(STENCIL_EINVAL, "max_slots, chunk_steps >= 1");
+    if (!(cfg->hbm_budget_frac > 0) && cfg->hbm_budget_bytes <= 0)
+        return fail(STENCIL_EINVAL, "need a memory budget");
+    if (cfg->storage != STENCIL_FP32 && cfg->storage != STENCIL_FP16 && cfg->storage != STENCIL_BF16)
+        return fail(STENCIL_EINVAL, "bad storage");
+    auto s = std::make_unique<Server>();
+    s->cfg = *cfg;
+    cudaError_t e = cudaGetDevice(&s->dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(STENCIL_ENODEV, "no CUDA device: %s", cudaGetErrorString(e));
+    }
+    size_t free_b = 0, total_b = 0;
+    if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return fail_cuda(e, "cudaMemGetInfo");
+    s->budget = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes
+                                          : (int64_t)(cfg->hbm_budget_frac * (double)total_b);
+    stencil_tile t = cfg->tile;
+    if (t.kernel == STENCIL_KERNEL_AUTO) t = stencil_tile{STENCIL_KERNEL_TILED, 64, 16, 0};
+    if (t.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EUNSUPPORTED, "the server runs the tiled kernel");
+    TiledInfo info;
+    if (!tiled_config(cfg->radius, cfg->storage, t.tx, t.ty, &info))
+        return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not built", t.tx, t.ty);
+    if (cfg->cuda_stream) {
+        s->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return fail_cuda(e, "cudaStreamCreate");
+        s->own_stream = true;
+    }
+    s->group.R = cfg->radius;
+    s->group.storage = cfg->storage;
+    s->group.tx = t.tx;
+    s->group.ty = t.ty;
+    s->group.stream = s->stream;
+    s->group.graph_len = 0;
+    if ((e = cudaStreamCreateWithFlags(&s->retire_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return fail_cuda(e, "cudaStreamCreate(retire)");
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->dev;
+    if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) {
+        cudaStreamDestroy(s->retire_stream);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return fail_cuda(e, "cudaMemPoolCreate");
+    }
+    for (int k = 0; k < 2; ++k) {
+        if ((e = cudaMallocHost(reinterpret_cast<void **>(&s->bounce[k]), Server::BOUNCE_BYTES)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&s->bounce_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+            for (int j = 0; j <= k; ++j) {
+                if (s->bounce[j]) cudaFreeHost(s->bounce[j]);
+                if (s->bounce_ev[j]) cudaEventDestroy(s->bounce_ev[j]);
+            }
+            cudaMemPoolDestroy(s->pool);
+            cudaStreamDestroy(s->retire_stream);
+            if (s->own_stream) cudaStreamDestroy(s->stream);
+            return fail_cuda(e, "pinned read-back buffers");
+        }
+    }
+    uint64_t keep = (uint64_t)s->budget;                 // keep freed memory for the next shots
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    s->stats.budget_bytes = s->budget;
+    s->t0 = Clock::now();
+    Server *raw = s.get();
+    s->engine = std::thread([raw] { raw->run(); });
+    s->retirer = std::thread([raw] { raw->retire_loop(); });
+    *out = reinterpret_cast<shot_server_t>(s.release());
+    return STENCIL_OK;
+}
+
+int shot_submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float *out_host, uint64_t *ticket)
+{
+    if (!h || !d || !ticket) return fail(STENCIL_EINVAL, "null argument");
+    if (nsteps < 0) return fail(STENCIL_EINVAL, "nsteps < 0");
+    Server *s = reinterpret_cast<Server *>(h);
+    if (d->radius != s->cfg.radius) return fail(STENCIL_EINVAL, "radius differs from the server's");
+    if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || !d->velocity) return fail(STENCIL_EINVAL, "bad descriptor");
+    auto r = std::make_unique<Request>();
+    r->desc = *d;
+    r->desc.storage = s->cfg.storage;
+    r->nsteps = nsteps;
+    r->out_host = out_host;
+    r->bytes = projected_bytes(r->desc);
+    if (!d->velocity_on_device) {
+        // the request keeps its own copy of the model until admission
+        const size_t n = (size_t)d->nx * d->ny * d->nz;
+        r->velocity.assign(d->velocity, d->velocity + n);
+        r->desc.velocity = r->velocity.data();
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->stopping) return fail(STENCIL_ECANCELLED, "the server is shutting down");
+    r->ticket = s->next_ticket++;
+    r->t_submit = s->now();
+    *ticket = r->ticket;
+    s->stats.submitted += 1;
+    if (r->bytes > s->budget) {
+        r->state = SHOT_FAILED;
+        r->status = STENCIL_EBUDGET;
+        r->t_done = r->t_submit;
+        s->stats.failed += 1;
+        s->all[r->ticket] = std::move(r);
+        return fail(STENCIL_EBUDGET, "shot needs more device memory than the whole budget");
+    }
+    s->stats.queued += 1;
+    s->queue.push_back(r.get());
+    s->all[r->ticket] = std::move(r);
+    s->cv.notify_all();
+    return STENCIL_OK;
+}
+
+int shot_poll(shot_server_t h, uint64_t ticket, int32_t *state, shot_timing *t)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null server");
+    Server *s = reinterpret_cast<Server *>(h);
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return fail(STENCIL_EUNKNOWN_TICKET, "no shot with ticket %llu", (unsigned long long)ticket);
+    const Request *r = it->second.get();
+    if (state) *state = r->state;
+    if (t) {
+        t->t_submit = r->t_submit;
+        t->t_admit = r->t_admit;
+        t->t_done = r->t_done;
+        t->steps_done = r->steps_done;
+        t->status = r->status;
+        t->pad = 0;
+    }
+    return STENCIL_OK;
+}
+
+int shot_wait(shot_server_t h, uint64_t ticket, double timeout_s, int32_t *state)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null server");
+    Server *s = reinterpret_cast<Server *>(h);
+    std::unique_lock<std::mutex> lock(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return fail(STENCIL_EUNKNOWN_TICKET, "no shot with ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second.get();
+    const auto until = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(timeout_s));
+    const bool finished = s->cv.wait_until(lock, until, [&] { return r->state == SHOT_DONE || r->state == SHOT_FAILED; });
+    if (state) *state = r->state;
+    if (!finished) return fail(STENCIL_ENOTREADY, "shot %llu not finished", (unsigned long long)ticket);
+    return STENCIL_OK;
+}
+
+int shot_server_get_stats(shot_server_t h, shot_server_stats *out)
+{
+    if (!h || !out) return fail(STENCIL_EINVAL, "null argument");
+    Server *s = reinterpret_cast<Server *>(h);
+    std::lock_guard<std::mutex> lock(s->mu);
+    *out = s->stats;
+    return STENCIL_OK;
+}
+
+int shot_server_destroy(shot_server_t h)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null server");
+    Server *s = reinterpret_cast<Server *>(h);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->stopping = true;
+    }
+    s->cv.notify_all();
+    if (s->engine.joinable()) s->engine.join();
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->retire_stop = true;
+    }
+    s->cv.notify_all();
+    if (s->retirer.joinable()) s->retirer.join();
+    cudaSetDevice(s->dev);
+    s->group.release();
+    cudaStreamSynchronize(s->retire_stream);
+    cudaStreamDestroy(s->retire_stream);
+    for (int k = 0; k < 2; ++k) {
+        if (s->bounce[k]) cudaFreeHost(s->bounce[k]);
+        if (s->bounce_ev[k]) cudaEventDestroy(s->bounce_ev[k]);
+    }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    const int err = s->engine_error;
+    delete s;
+    return err;
+}
+
+}  // extern "C"

@@ -155,13 +155,15 @@ __device__ __forceinline__ float4 scale4(const float4 &v, float s)
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// One block's work: tile (bx, by) of the xy plane, output planes [z0, z1)
+// of one shot, at time level n.  map_* are the shot's tensor maps (kernel
+// parameters or 64-byte aligned global memory).
 template <int R, int TX, int TY, typename E>
-__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
-    sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,
-                       const __grid_constant__ CUtensorMap map_k, const SweepParams p)
+__device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUtensorMap *map_up,
+                                           const CUtensorMap *map_k, const SweepParams &p, int bx, int by,
+                                           int z0, int z1, int64_t n_level, unsigned char *smem)
 {
     using S = TiledShape<R, TX, TY, E>;
-    extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *su = smem;
     unsigned char *sp = smem + S::P_OFF;
     unsigned char *sk = smem + S::K_OFF;
@@ -174,12 +176,8 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + S::FLAG_OFF);
 
     const int tid = threadIdx.x;
-    const int bx = blockIdx.x % p.tiles_x;
-    const int by = blockIdx.x / p.tiles_x;
     const int x0 = bx * TX;
     const int y0 = by * TY;
-    const int z0 = blockIdx.y * p.zchunk;
-    const int z1 = min(z0 + p.zchunk, p.nz);
     if (z0 >= z1) return;                     // uniform over the block
     const int nout = z1 - z0;                 // output planes
     const int nin = nout + 2 * R;             // planes through the ring: z0-R .. z1+R-1
@@ -188,13 +186,13 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
     auto issue_u = [&](int t) {               // plane pz0 + t into stage t % SU
         const int st = t % S::SU;
         mbar_arrive_expect_tx(&full_u[st], S::U_BYTES);
-        tma_load_3d(su + st * S::U_STAGE, &map_u, &full_u[st], x0 - S::HX, y0 - R, pz0 + t);
+        tma_load_3d(su + st * S::U_STAGE, map_u, &full_u[st], x0 - S::HX, y0 - R, pz0 + t);
     };
     auto issue_a = [&](int ja) {              // u^{n-1} and kappa of output z0 + ja into stage ja % SA
         const int st = ja % S::SA;
         mbar_arrive_expect_tx(&full_a[st], S::P_BYTES + S::K_BYTES);
-        tma_load_3d(sp + st * S::P_STAGE, &map_up, &full_a[st], x0, y0, z0 + ja);
-        tma_load_3d(sk + st * S::K_STAGE, &map_k, &full_a[st], x0, y0, z0 + ja);
+        tma_load_3d(sp + st * S::P_STAGE, map_up, &full_a[st], x0, y0, z0 + ja);
+        tma_load_3d(sk + st * S::K_STAGE, map_k, &full_a[st], x0, y0, z0 + ja);
     };
 
     if (tid == 0) {
@@ -209,7 +207,7 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
     if constexpr (!S::F32) {
         // scales of this block's planes, and those of its outputs (every block
         // computes the same value; tile 0 of each z-chunk publishes them)
-        const int64_t n = current_step(p);
+        const int64_t n = n_level;
         const int s_n = (int)(n & 3), s_p = (int)((n + 3) & 3);
         slot_out = (int)((n + 1) & 3);
         const int s_clear = (int)((n + 2) & 3);
@@ -231,10 +229,10 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
             if (p.src.on && o == p.src.z) b += p.src_bound;
             const float sg = pow2_scale(b);
             sig_out[j] = sg;
-            if (blockIdx.x == 0) p.scale[(int64_t)slot_out * p.nz + o] = sg;
+            if (bx == 0 && by == 0) p.scale[(int64_t)slot_out * p.nz + o] = sg;
         }
         // level n-2's slot becomes level n+2's: clear it for the next step
-        if (blockIdx.x == 0 && blockIdx.y == 0)
+        if (bx == 0 && by == 0 && z0 == 0)
             for (int z = tid; z < p.nz; z += S::NT) p.amax[(int64_t)s_clear * p.nz + z] = 0u;
     }
     __syncthreads();
@@ -407,7 +405,7 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
                         __ffma2_rn(hi2(kap[h]), fB, __ffma2_rn(neg1, hi2(prev[h]), __fmul2_rn(two, hi2(cc))));
                     float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
                     if (src_here && src_row == h && o == p.src.z) {
-                        const double t = (double)current_step(p) * p.src.dt;
+                        const double t = (double)n_level * p.src.dt;
                         const float add = (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
                         const int k = p.src.x - gx;
                         if (k == 0) nxt.x += add;
@@ -471,6 +469,46 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
         for (int ja = cons_a; ja < iss_a; ++ja)
             mbar_wait(&full_a[ja % S::SA], (ja / S::SA) & 1, p.err, 100000000ull);
     }
+}
+
+// One shot per launch: block (tile, z-chunk) from the grid position.
+template <int R, int TX, int TY, typename E>
+__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
+    sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,
+                       const __grid_constant__ CUtensorMap map_k, const SweepParams p)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int bx = blockIdx.x % p.tiles_x;
+    const int by = blockIdx.x / p.tiles_x;
+    const int z0 = blockIdx.y * p.zchunk;
+    const int z1 = min(z0 + p.zchunk, p.nz);
+    sweep_tile<R, TX, TY, E>(&map_u, &map_up, &map_k, p, bx, by, z0, z1, current_step(p), smem);
+}
+
+// Many shots per launch (one time step of each): block b does work item
+// items[b] of shot items[b].shot.  A shot whose step counter has reached its
+// last step is left as it is (its blocks return at once), so shots with
+// different step counts share one launch sequence.
+template <int R, int TX, int TY, typename E>
+__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
+    sweep_grouped_kernel(const GroupShot *shots, const GroupItem *items, int step_off)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const GroupItem it = items[blockIdx.x];
+    const GroupShot &g = shots[it.shot];
+    const int64_t n = *g.prm.step_base + step_off;
+    if (n >= g.n_end) return;                       // uniform over the block
+    const int par = (int)((n + g.parity_base) & 1);
+    SweepParams p = g.prm;
+    p.u = g.buf[par];
+    p.up = g.buf[par ^ 1];
+    p.step_off = step_off;
+    if (threadIdx.x == 0) {                         // the copy-issuing thread
+        fence_tensormap(&g.halo[par]);
+        fence_tensormap(&g.core[par ^ 1]);
+        fence_tensormap(&g.kcore);
+    }
+    sweep_tile<R, TX, TY, E>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n, smem);
 }
 
 }  // namespace stencil

@@ -23,4 +23,11 @@ cudaError_t launch_tiled_f32(int R, int tx, int ty, const TiledMaps &m, const Sw
     STENCIL_TILE_SWITCH(float, TILES_F32, return I::launch(m, p, s), return cudaErrorInvalidConfiguration);
 }
 
+cudaError_t launch_grouped_f32(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
+                              int step_off, cudaStream_t s)
+{
+    STENCIL_TILE_SWITCH(float, TILES_F32, return I::launch_grouped(shots, items, n_items, step_off, s),
+                        return cudaErrorInvalidConfiguration);
+}
+
 }  // namespace stencil

@@ -27,6 +27,9 @@ struct Inst {
             std::call_once(once, [] {
                 status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+                if (status == cudaSuccess)
+                    status = cudaFuncSetAttribute(sweep_grouped_kernel<R, TX, TY, E>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
             });
             return status;
         }
@@ -73,6 +76,20 @@ struct Inst {
             q.zchunk = zc;
             dim3 grid(tiles_x * tiles_y, nzc);
             sweep_tiled_kernel<R, TX, TY, E><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
+            return cudaGetLastError();
+        }
+    }
+
+    static cudaError_t launch_grouped(const GroupShot *shots, const GroupItem *items, int n_items, int step_off,
+                                      cudaStream_t s)
+    {
+        if constexpr (!fits) {
+            return cudaErrorInvalidConfiguration;
+        } else {
+            cudaError_t e = prepare();
+            if (e != cudaSuccess) return e;
+            if (n_items <= 0) return cudaSuccess;
+            sweep_grouped_kernel<R, TX, TY, E><<<n_items, S::NT, S::SMEM, s>>>(shots, items, step_off);
             return cudaGetLastError();
         }
     }

@@ -1,0 +1,198 @@
+"""Batched shots (one grouped launch per step) and the continuous-batching
+shot server: every shot's result is bit-identical to the same shot run alone
+through stencil_run, and matches the FP64 oracle."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1310_8232_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1310_8232_gb300 import binding as st
+    torch.cuda.set_device(0)
+    torch.cuda.set_stream(torch.cuda.Stream())
+    return torch, st
+
+
+def stream(torch):
+    return torch.cuda.current_stream().cuda_stream
+
+
+SHAPES = [(67, 45, 33), (96, 64, 40), (40, 40, 40), (130, 20, 51), (33, 97, 12), (64, 64, 64)]
+
+
+def shot(i, shape, R=5, storage=0):
+    nx, ny, nz = shape
+    v = workloads.layered_velocity(nx, ny, nz, n_layers=4, seed=100 + i)
+    dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
+    src = (nx // 3, ny // 2, nz // 2)
+    return v, dt, src
+
+
+def alone(env, v, dt, src, steps, R=5, storage=0):
+    torch, st = env
+    plan = st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, storage=storage, stream=stream(torch)))
+    try:
+        out = np.empty_like(v)
+        st.stencil_run(plan, steps, out)
+    finally:
+        st.stencil_destroy(plan)
+    return out
+
+
+@pytest.mark.parametrize("graph", [0, 6])
+def test_batch_shots_equal_alone_runs(env, graph):
+    torch, st = env
+    shots = [shot(i, s) for i, s in enumerate(SHAPES)]
+    descs = [st.make_desc(v, dt, radius=5, src=src, stream=stream(torch)) for v, dt, src in shots]
+    batch = st.stencil_batch_create(descs, graph_steps=graph)
+    try:
+        assert st.stencil_batch_size(batch) == len(shots)
+        st.stencil_batch_run(batch, 17)
+        st.stencil_batch_run(batch, 13)
+        st.stencil_batch_sync(batch)
+        outs = []
+        for i, (v, dt, src) in enumerate(shots):
+            out = np.empty_like(v)
+            plan = st.stencil_batch_plan(batch, i)
+            st.stencil_get_field(plan, 0, out)
+            assert st.stencil_get_stats(plan).steps_done == 30
+            outs.append(out)
+    finally:
+        st.stencil_batch_destroy(batch)
+    for (v, dt, src), out in zip(shots, outs):
+        assert np.array_equal(out, alone(env, v, dt, src, 30))
+        ref, _ = oracle.run(v, workloads.DX, dt, 5, 30, src=src)
+        assert oracle.rel_l2(out, ref) <= 1e-5
+
+
+def test_batch_16bit_equals_alone(env):
+    torch, st = env
+    shots = [shot(i, s) for i, s in enumerate(SHAPES[:3])]
+    descs = [st.make_desc(v, dt, radius=4, src=src, storage=1, stream=stream(torch)) for v, dt, src in shots]
+    batch = st.stencil_batch_create(descs, graph_steps=4)
+    try:
+        st.stencil_batch_run(batch, 22)
+        outs = []
+        for i, (v, dt, src) in enumerate(shots):
+            out = np.empty_like(v)
+            st.stencil_get_field(st.stencil_batch_plan(batch, i), 0, out)
+            outs.append(out)
+    finally:
+        st.stencil_batch_destroy(batch)
+    for (v, dt, src), out in zip(shots, outs):
+        assert np.array_equal(out, alone(env, v, dt, src, 22, R=4, storage=1))
+
+
+def test_batch_rejects_mixed_radius(env):
+    torch, st = env
+    (v, dt, src) = shot(0, SHAPES[0])
+    d1 = st.make_desc(v, dt, radius=5, src=src)
+    d2 = st.make_desc(v, dt, radius=4, src=src)
+    with pytest.raises(st.StencilError) as ei:
+        st.stencil_batch_create([d1, d2])
+    assert ei.value.code == st.STENCIL_EINVAL
+
+
+def make_server(st, **kw):
+    cfg = st.shot_server_cfg_init()
+    cfg.radius = kw.pop("radius", 5)
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return st.shot_server_create(cfg)
+
+
+def test_server_results_identical_to_alone_and_mixed_arrivals(env):
+    torch, st = env
+    server = make_server(st, chunk_steps=7, max_slots=4)
+    rng = np.random.default_rng(7)
+    jobs = []
+    try:
+        for i, shape in enumerate(SHAPES + SHAPES[:2]):
+            v, dt, src = shot(i, shape)
+            steps = int(rng.integers(5, 40))
+            out = np.full_like(v, np.nan)
+            d = st.make_desc(v, dt, radius=5, src=src)
+            t = st.shot_submit(server, d, steps, out)
+            jobs.append((t, v, dt, src, steps, out))
+            time.sleep(0.002 * (i % 3))            # arrivals while others run
+        for t, *_ in jobs:
+            assert st.shot_wait(server, t, 120.0) == st.SHOT_DONE
+        stats = st.shot_server_get_stats(server)
+        assert stats.done == len(jobs) and stats.failed == 0 and stats.running == 0
+        for t, v, dt, src, steps, out in jobs:
+            state, tm = st.shot_poll(server, t)
+            assert state == st.SHOT_DONE and tm.steps_done == steps
+            assert 0 <= tm.t_submit <= tm.t_admit <= tm.t_done
+    finally:
+        st.shot_server_destroy(server)
+    for t, v, dt, src, steps, out in jobs:
+        assert np.array_equal(out, alone(env, v, dt, src, steps)), t
+
+
+def test_server_budget_queues_and_rejects(env):
+    torch, st = env
+    v, dt, src = shot(0, (64, 64, 64))
+    one = 64 * 64 * 64 * 12 + 200_000
+    server = make_server(st, hbm_budget_bytes=int(1.5 * one), chunk_steps=5)
+    try:
+        outs, tickets = [], []
+        for _ in range(3):                          # only one fits at a time: the rest queue
+            out = np.empty_like(v)
+            tickets.append(st.shot_submit(server, st.make_desc(v, dt, radius=5, src=src), 12, out))
+            outs.append(out)
+        big = workloads.constant_velocity(200, 200, 200, 2000.0)
+        with pytest.raises(st.StencilError) as ei:
+            st.shot_submit(server, st.make_desc(big, dt, radius=5), 3, np.empty_like(big))
+        assert ei.value.code == st.STENCIL_EBUDGET
+        for t in tickets:
+            assert st.shot_wait(server, t, 60.0) == st.SHOT_DONE
+        s = st.shot_server_get_stats(server)
+        assert s.failed == 1 and s.done == 3 and s.bytes_in_use == 0
+    finally:
+        st.shot_server_destroy(server)
+    ref = alone(env, v, dt, src, 12)
+    for out in outs:
+        assert np.array_equal(out, ref)
+
+
+def test_server_unknown_ticket_and_cancel_on_destroy(env):
+    torch, st = env
+    server = make_server(st, chunk_steps=2, max_slots=1)
+    v, dt, src = shot(1, (96, 64, 40))
+    outs = [np.empty_like(v) for _ in range(4)]
+    tickets = [st.shot_submit(server, st.make_desc(v, dt, radius=5, src=src), 400, o) for o in outs]
+    with pytest.raises(st.StencilError) as ei:
+        st.shot_poll(server, 987654)
+    assert ei.value.code == st.STENCIL_EUNKNOWN_TICKET
+    st.shot_server_destroy(server)        # finishes the admitted shot, cancels the queued ones
+
+
+def test_server_shot_with_invalid_model_fails_cleanly(env):
+    torch, st = env
+    server = make_server(st)
+    try:
+        v, dt, src = shot(2, (40, 40, 40))
+        bad = v.copy()
+        bad[3, 3, 3] = -1.0
+        t = st.shot_submit(server, st.make_desc(bad, dt, radius=5, src=src), 10, np.empty_like(v))
+        assert st.shot_wait(server, t, 30.0) == st.SHOT_FAILED
+        state, tm = st.shot_poll(server, t)
+        assert tm.status == st.STENCIL_EINVAL
+        good = np.empty_like(v)
+        t2 = st.shot_submit(server, st.make_desc(v, dt, radius=5, src=src), 10, good)
+        assert st.shot_wait(server, t2, 30.0) == st.SHOT_DONE
+    finally:
+        st.shot_server_destroy(server)
+    assert np.array_equal(good, alone(env, v, dt, src, 10))
