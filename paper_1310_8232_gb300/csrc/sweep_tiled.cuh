@@ -125,6 +125,9 @@ struct TiledShape {
     static_assert(TX % 32 == 0 && TX >= 32 && BW <= 256 && BH <= 256, "TMA box limits");
     static_assert(TY % ROWS == 0, "whole thread rows");
     static constexpr bool VALID = NT <= 1024 && NT % 32 == 0;
+    // blocks per SM the register allocation is held to: three 128-thread
+    // blocks per SM are what keep enough planes in flight (<= 170 registers)
+    static constexpr int MINB = NT == 128 ? 3 : 1;
 };
 
 // compile-time loop: f(integral_constant<K>) for K = 0..N-1
@@ -160,10 +163,13 @@ __device__ __forceinline__ float4 scale4(const float4 &v, float s)
 // parameters or 64-byte aligned global memory).
 template <int R, int TX, int TY, typename E>
 __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUtensorMap *map_up,
-                                           const CUtensorMap *map_k, const SweepParams &p, int bx, int by,
+                                           const CUtensorMap *map_k, const SweepParams &params, int bx, int by,
                                            int z0, int z1, int64_t n_level, unsigned char *smem)
 {
     using S = TiledShape<R, TX, TY, E>;
+    // a private copy: the inline-asm waits and copies clobber memory, which
+    // would otherwise force every field to be reloaded after each of them
+    const SweepParams p = params;
     unsigned char *su = smem;
     unsigned char *sp = smem + S::P_OFF;
     unsigned char *sk = smem + S::K_OFF;
@@ -473,7 +479,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
 
 // One shot per launch: block (tile, z-chunk) from the grid position.
 template <int R, int TX, int TY, typename E>
-__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
+__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
     sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,
                        const __grid_constant__ CUtensorMap map_k, const SweepParams p)
 {
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
 // last step is left as it is (its blocks return at once), so shots with
 // different step counts share one launch sequence.
 template <int R, int TX, int TY, typename E>
-__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT)
+__global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
     sweep_grouped_kernel(const GroupShot *shots, const GroupItem *items, int step_off)
 {
     extern __shared__ __align__(128) unsigned char smem[];

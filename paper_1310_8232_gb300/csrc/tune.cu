@@ -117,12 +117,18 @@ struct Cand {
 static const int TX_VALUES[] = {32, 64, 128};
 static const int TY_VALUES[] = {4, 8, 16, 32};
 
-// z-chunks 8, 16, 32, ... below nz, then nz (capped for 16-bit storage)
+// z-chunks 8, 12, 16, 24, 32, 48, ... (powers of two and 1.5x them) below
+// top, then top = min(nz, zmax) (zmax: the 16-bit kernels' bound; for the
+// slab-based selections the slab depth, since a chunk deeper than a slab
+// cannot be timed there)
 static std::vector<int> zchunk_values(int nz, int zmax)
 {
     const int top = zmax > 0 ? std::min(nz, zmax) : nz;
     std::vector<int> z;
-    for (int v = 8; v < top; v *= 2) z.push_back(v);
+    for (int v = 8; v < top; v *= 2) {
+        z.push_back(v);
+        if (v + v / 2 < top) z.push_back(v + v / 2);
+    }
     z.push_back(top);
     return z;
 }
@@ -147,8 +153,9 @@ static std::vector<Cand> admissible(int R, int storage, int nz)
     return out;
 }
 
-// The P-part candidate set of Sec. 3.7, one axis list per tile parameter.
-static std::vector<Cand> candidate_set(int R, int storage, int nz, int P)
+// The P-part candidate set of Sec. 3.7, one axis list per tile parameter;
+// z-chunks no deeper than `zcap` (the slab each selection stream sweeps).
+static std::vector<Cand> candidate_set(int R, int storage, int nz, int P, int zcap)
 {
     std::vector<int> txs(std::begin(TX_VALUES), std::end(TX_VALUES));
     std::vector<int> tys(std::begin(TY_VALUES), std::end(TY_VALUES));
@@ -156,8 +163,10 @@ static std::vector<Cand> candidate_set(int R, int storage, int nz, int P)
     int zmax = 0;
     for (int tx : pick_axis(txs, P))
         for (int ty : pick_axis(tys, P))
-            if (feasible(R, storage, tx, ty, &zmax))
-                for (int zc : pick_axis(zchunk_values(nz, zmax), P)) out.push_back({tx, ty, zc});
+            if (feasible(R, storage, tx, ty, &zmax)) {
+                const int cap = zmax > 0 ? std::min(zmax, zcap) : zcap;
+                for (int zc : pick_axis(zchunk_values(nz, cap), P)) out.push_back({tx, ty, zc});
+            }
     return out;
 }
 
@@ -292,7 +301,7 @@ int tune_plan(Plan *p, const stencil_desc *d)
 
     std::vector<Cand> cands = (mode == STENCIL_TUNE_EXHAUSTIVE || mode == STENCIL_TUNE_OWN)
                                   ? admissible(p->R, p->storage, p->nz)
-                                  : candidate_set(p->R, p->storage, p->nz, P);
+                                  : candidate_set(p->R, p->storage, p->nz, P, std::max(1, p->nz / C));
     if (cands.empty()) return fail(STENCIL_EUNSUPPORTED, "no feasible tile");
     Cand chosen{};
     double min_ms = 0, actual_ms = 0;
