@@ -223,13 +223,18 @@ def run_reference(args):
     }), flush=True)
 
 
-def run_batch(args, torch, st, workloads, clk_index):
+def run_batch(args, torch, st, workloads, ranks):
     """64 shots with uneven grids (each dim in {96, 128, ..., 320}, seed 4064),
     8-layer random models, 100 steps each: one grouped launch per step
-    (graph-captured) against a loop of per-shot plans."""
+    (graph-captured) against a loop of per-shot plans.  On N GPUs every rank
+    takes a contiguous share of the 64 shots (fixed total: strong scaling)."""
     R, T = args.radius, args.timesteps if args.timesteps != 200 else 100
-    dims = workloads.batch_dims(args.shots)
-    seeds = workloads.batch_layer_seeds(args.shots)
+    all_dims = workloads.batch_dims(args.shots)
+    if args.shots < ranks.env.world:
+        raise SystemExit("batch: need at least one shot per rank")
+    lo, hi = ranks.shard(args.shots)
+    dims = all_dims[lo:hi]
+    seeds = workloads.batch_layer_seeds(args.shots)[lo:hi]
     stream = torch.cuda.current_stream()
     descs, vels = [], []
     for (nx, ny, nz), sd in zip(dims, seeds):
@@ -237,7 +242,7 @@ def run_batch(args, torch, st, workloads, clk_index):
         dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(v.max()))
         vels.append(v)
         descs.append(st.make_desc(v, dt, radius=R, dx=workloads.DX, graph_steps=20, stream=stream.cuda_stream))
-    pts = float(sum(nx * ny * nz for nx, ny, nz in dims)) * T
+    pts = float(sum(nx * ny * nz for nx, ny, nz in all_dims)) * T
     batch = st.stencil_batch_create(descs, graph_steps=20)
     plans = [st.stencil_plan(d) for d in descs]
 
@@ -259,17 +264,17 @@ def run_batch(args, torch, st, workloads, clk_index):
         run_grouped()
         run_loop()
     torch.cuda.synchronize()
-    with ClockSampler(clk_index) as clk:
+    with ClockSampler(ranks.env.local) as clk:
         for _ in range(args.steps):
             for name, fn in (("grouped", run_grouped), ("loop", run_loop)):
                 reset()
-                torch.cuda.synchronize()
+                ranks.barrier()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 fn()
                 b.record(stream)
-                torch.cuda.synchronize()
-                times[name].append(a.elapsed_time(b))
+                ranks.barrier()
+                times[name].append(ranks.max(a.elapsed_time(b)))
     zc = st.stencil_batch_zchunk(batch)
     st.stencil_batch_sync(batch)
     st.stencil_batch_destroy(batch)
@@ -277,13 +282,17 @@ def run_batch(args, torch, st, workloads, clk_index):
         st.stencil_destroy(p)
     g_ms = sum(times["grouped"]) / len(times["grouped"])
     l_ms = sum(times["loop"]) / len(times["loop"])
+    if not ranks.is_root:
+        return
     line = {
-        "metric": METRIC, "value": pts / (g_ms / 1e3) / 1e9, "unit": METRIC, "n_gpus": 1,
+        "metric": METRIC, "value": pts / (g_ms / 1e3) / 1e9, "unit": METRIC, "n_gpus": ranks.env.world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": g_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch of {len(dims)} shots, dims uniform in {{96..320 step 32}} (seed 4064), "
+        "scaling": "strong" if ranks.env.world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"batch of {len(all_dims)} shots, dims uniform in {{96..320 step 32}} (seed 4064), "
                                f"8-layer random models, R={R}, {T} steps each; one grouped launch per step, "
-                               f"20-step CUDA graphs", "shots": len(dims), "timesteps": T,
+                               f"20-step CUDA graphs", "shots": len(all_dims), "timesteps": T,
+                   "parallelism": f"replicas: contiguous shot shares over {ranks.env.world} GPU(s)",
                    "point_updates": pts, "zchunk": zc},
         "per_shot_loop": {"value": pts / (l_ms / 1e3) / 1e9, "ms_per_step": l_ms,
                           "what": "the same shots, one plan each, stencil_step(100) in a loop (20-step graphs)"},
@@ -299,14 +308,16 @@ def run_batch(args, torch, st, workloads, clk_index):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args, torch, st, workloads, clk_index):
+def run_serve(args, torch, st, workloads, ranks):
     """Open-loop Poisson arrivals (seed 5020, mean --rate per second) over
     --window seconds: cube side log-uniform on [64, 400], steps uniform on
     [50, 500], FP32, 8-layer random models, admitted under an 80 % HBM
-    budget; reports throughput and p50 / p99 latency (done - submit)."""
+    budget; reports throughput and p50 / p99 latency (done - submit).  On N
+    GPUs the arrivals are dealt round-robin, one shot server per GPU."""
     import numpy as np
     R = args.radius
-    arrivals = workloads.poisson_arrivals(args.rate, args.window)
+    all_arrivals = workloads.poisson_arrivals(args.rate, args.window)
+    arrivals = all_arrivals[ranks.env.rank::ranks.env.world]
     cfg = st.shot_server_cfg_init()
     cfg.radius = R
     cfg.chunk_steps = 20
@@ -324,11 +335,11 @@ def run_serve(args, torch, st, workloads, clk_index):
         dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(vl_host.max()))
         out = np.empty((n, n, n), dtype=np.float32)
         reqs.append((a, v, st.make_desc(v, dt, radius=R, dx=workloads.DX), out))
-    torch.cuda.synchronize()
+    ranks.barrier()
     jobs = []
     submit_s = 0.0
     t_start = time.perf_counter()
-    with ClockSampler(clk_index) as clk:
+    with ClockSampler(ranks.env.local) as clk:
         for a, v, d, out in reqs:
             delay = a["t"] - (time.perf_counter() - t_start)
             if delay > 0:
@@ -340,41 +351,55 @@ def run_serve(args, torch, st, workloads, clk_index):
         for t, *_ in jobs:
             st.shot_wait(server, t, 600.0)
     stats = st.shot_server_get_stats(server)
-    lat, queue_s, service, t_first, t_last, pts = [], [], [], None, None, 0.0
+    mine = []
     for t, n, steps, v, out in jobs:
         state, tm = st.shot_poll(server, t)
         if state != st.SHOT_DONE:
             continue
-        lat.append(tm.t_done - tm.t_submit)
-        queue_s.append(tm.t_admit - tm.t_submit)
-        service.append(tm.t_done - tm.t_admit)
-        t_first = tm.t_submit if t_first is None else min(t_first, tm.t_submit)
-        t_last = tm.t_done if t_last is None else max(t_last, tm.t_done)
-        pts += float(n) ** 3 * steps
+        mine.append((tm.t_submit, tm.t_admit, tm.t_done, float(n) ** 3 * steps))
     st.shot_server_destroy(server)
+    pooled = ranks.gather({"shots": mine, "stats": (stats.done, stats.failed, stats.iterations, stats.busy_s,
+                                                    stats.admit_s, stats.build_s, stats.retire_s),
+                           "submit_s": submit_s})
+    if not ranks.is_root:
+        return
+    # the ranks start together (barrier); the job spans the longest rank's
+    # first-submit to last-done interval
+    lat, queue_s, service, pts, span = [], [], [], 0.0, 0.0
+    for part in pooled:
+        for ts, ta, td, p in part["shots"]:
+            lat.append(td - ts)
+            queue_s.append(ta - ts)
+            service.append(td - ta)
+            pts += p
+        if part["shots"]:
+            span = max(span, max(s[2] for s in part["shots"]) - min(s[0] for s in part["shots"]))
+    span = span or None
+    submit_s = sum(part["submit_s"] for part in pooled)
+    agg = [sum(part["stats"][i] for part in pooled) for i in range(7)]
     lat_s = sorted(lat)
 
     def pct(xs, q):
         return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))] if xs else None
 
-    span = (t_last - t_first) if lat else None
     line = {
         "metric": "shot latency p50/p99 (s) and throughput", "value": pts / span / 1e9 if span else None,
-        "unit": METRIC, "n_gpus": 1, "steps": len(lat), "warmup": 0,
+        "unit": METRIC, "n_gpus": ranks.env.world, "steps": len(lat), "warmup": 0,
         "ms_per_step": 1e3 * statistics.mean(lat) if lat else None, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "strong" if ranks.env.world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
         "config": {"workload": f"Poisson arrivals, mean {args.rate}/s over {args.window} s (seed 5020), "
                                f"cube side log-uniform 64-400, steps uniform 50-500, R={R}, "
                                "8-layer random models, 80% HBM budget, 20 steps per engine iteration",
-                   "shots": len(arrivals)},
+                   "shots": len(all_arrivals),
+                   "parallelism": f"replicas: arrivals dealt round-robin to {ranks.env.world} shot server(s)"},
         "latency_s": {"p50": pct(lat_s, 0.50), "p99": pct(lat_s, 0.99), "mean": statistics.mean(lat) if lat else None},
         "queue_s": {"mean": statistics.mean(queue_s) if queue_s else None,
                     "p99": pct(sorted(queue_s), 0.99)},
         "service_s": {"mean": statistics.mean(service) if service else None},
-        "offered_gpts_per_s": sum(float(a["side"]) ** 3 * a["steps"] for a in arrivals) / args.window / 1e9,
-        "server": {"done": stats.done, "failed": stats.failed, "iterations": stats.iterations,
-                   "busy_s": stats.busy_s, "admit_s": stats.admit_s, "build_s": stats.build_s,
-                   "retire_s": stats.retire_s, "submit_s": submit_s},
+        "offered_gpts_per_s": sum(float(a["side"]) ** 3 * a["steps"] for a in all_arrivals) / args.window / 1e9,
+        "server": {"done": agg[0], "failed": agg[1], "iterations": agg[2], "busy_s": agg[3],
+                   "admit_s": agg[4], "build_s": agg[5], "retire_s": agg[6], "submit_s": submit_s},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -387,31 +412,30 @@ def main():
         return
     if args.workload != "single":
         import torch
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+
+        from paper_1310_8232_gb300.replicas import Ranks, rank_env
+        env = rank_env()
+        torch.cuda.set_device(env.local)
+        ranks = Ranks(env)
         torch.cuda.set_stream(torch.cuda.Stream())
         import __graft_entry__
         __graft_entry__.build_library()
         from paper_1310_8232_gb300 import binding as st
         from paper_1310_8232_gb300 import workloads
         fn = run_batch if args.workload == "batch" else run_serve
-        fn(args, torch, st, workloads, int(os.environ.get("LOCAL_RANK", "0")))
+        fn(args, torch, st, workloads, ranks)
+        ranks.close()
         return
     import numpy as np
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1310_8232_gb300.replicas import Ranks, rank_env
 
-    def barrier():
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
+    env = rank_env()
+    world, rank, local = env.world, env.rank, env.local
+    torch.cuda.set_device(local)
+    ranks = Ranks(env)             # replicas: a barrier and a max over ranks, no data exchange
+    barrier = ranks.barrier
 
     import __graft_entry__
     __graft_entry__.build_library()
@@ -476,10 +500,7 @@ def main():
     st.stencil_sync(plan)
     elapsed_ms = start.elapsed_time(end)
     sweep_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms = ranks.max(elapsed_ms)
     pts_per_shot = float(n) ** 3 * T
     value = world * pts_per_shot * args.steps / (elapsed_ms / 1e3) / 1e9
     kernel_ms = sweep_ms / (args.steps * T)
@@ -509,10 +530,7 @@ def main():
             st.stencil_run(plan, T, hout)
         barrier()
         e2e_s = time.perf_counter() - t0
-        if dist:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = ranks.max(e2e_s)
         e2e = {"value": world * pts_per_shot * args.steps / e2e_s / 1e9, "unit": METRIC,
                "h2d_bytes_per_step": int(hv.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
                "api": "stencil_set_velocity(host pinned) + stencil_set_fields + stencil_run(out=host pinned)"}
@@ -546,8 +564,7 @@ def main():
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
