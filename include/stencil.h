@@ -129,6 +129,15 @@ typedef struct {
                                     non-blocking stream (the legacy default stream, handle 0,
                                     cannot be requested: graphs cannot be captured on it) */
     int32_t graph_steps;         /* steps per captured CUDA graph; 0 = launch step by step */
+    void   *user_buffers[3];     /* optional caller-owned device buffers, all three or none
+                                    (NULL = the plan allocates): [0] and [1] the two wavefield
+                                    levels, [2] kappa; each dense nx*ny*nz FP32 (x fastest),
+                                    16-byte aligned, and nx a multiple of 4 (the rows are TMA
+                                    strides), else STENCIL_EINVAL; FP32 storage only, else
+                                    STENCIL_EUNSUPPORTED.  The plan zeroes [0] and [1] (u^0 =
+                                    u^{-1} = 0) and writes kappa into [2]; u^n is then in
+                                    user_buffers[stats.current_buffer].  They stay the caller's
+                                    and must outlive the plan; the shot server does not take them. */
 } stencil_desc;
 
 /* Plan state, results of tuning and the device layout. */
@@ -151,6 +160,8 @@ typedef struct {
     double  selection_ms;        /* wall time spent selecting */
     int32_t n_candidates;        /* candidates timed */
     int32_t tune_mode;
+    int32_t current_buffer;      /* which of the plan's two field buffers holds u^n (0 or 1) */
+    int32_t user_buffers;        /* 1 if the plan runs on caller-owned buffers */
 } stencil_stats;
 
 typedef struct stencil_plan_s *stencil_plan_t;
@@ -205,6 +216,32 @@ STENCIL_API int stencil_set_fields(stencil_plan_t p, const float *u, const float
 STENCIL_API int stencil_set_velocity(stencil_plan_t p, const float *velocity, int32_t on_device);
 
 STENCIL_API int stencil_get_stats(stencil_plan_t p, stencil_stats *s);
+
+/* ---- checkpoint / restore ---------------------------------------------
+ * The time loop's state (Sec. 2, Algorithm 1): the two levels u^n and
+ * u^{n-1} in the plan's storage encoding, the step n (the source reads
+ * w(n dt)) and, for 16-bit storage, the per-plane scales and maxima of those
+ * two levels.  A plan restored from a checkpoint continues bit for bit as
+ * the plan that wrote it would have.  Format: a 128-byte header (magic
+ * "STNCKPT1", version 1, dims, radius, storage, element size, step, dx, dt,
+ * source position / frequency / delay / scale, payload bytes), then u^n and
+ * u^{n-1} dense (x fastest), then for 16-bit storage scale[n], scale[n-1]
+ * (nz floats each) and max[n], max[n-1] (nz uint32 each).  The velocity
+ * model is not included: restore into a plan made from the same descriptor
+ * (dims, radius, storage, dx, dt and source are checked, STENCIL_EINVAL on a
+ * mismatch; a different velocity model at the source point is caught, one
+ * elsewhere is not).  Tile and graph settings may differ. */
+
+/* Bytes stencil_checkpoint writes for this plan. */
+STENCIL_API int stencil_checkpoint_size(stencil_plan_t p, uint64_t *bytes);
+/* Write the state after everything enqueued so far into dst (bytes >=
+ * stencil_checkpoint_size, else STENCIL_EINVAL; on_device: dst is device
+ * memory).  Waits for the plan's stream; synchronous. */
+STENCIL_API int stencil_checkpoint(stencil_plan_t p, void *dst, uint64_t bytes, int32_t on_device);
+/* Replace the plan's state by the checkpoint in src (on_device: device
+ * memory); steps_done becomes the checkpoint's step.  Synchronous: src may
+ * be freed on return. */
+STENCIL_API int stencil_restore(stencil_plan_t p, const void *src, uint64_t bytes, int32_t on_device);
 
 /* ---- batches: many shots, one launch per time step --------------------- */
 

@@ -75,6 +75,7 @@ class stencil_desc(ctypes.Structure):
         ("storage", ctypes.c_int32), ("tune_mode", ctypes.c_int32),
         ("tile", stencil_tile), ("tune", stencil_tune_params),
         ("cuda_stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int32),
+        ("user_buffers", ctypes.c_void_p * 3),
     ]
 
 
@@ -87,6 +88,7 @@ class stencil_stats(ctypes.Structure):
         ("full_time_ms", ctypes.c_double),
         ("quality", ctypes.c_double), ("selection_ms", ctypes.c_double),
         ("n_candidates", ctypes.c_int32), ("tune_mode", ctypes.c_int32),
+        ("current_buffer", ctypes.c_int32), ("user_buffers", ctypes.c_int32),
     ]
 
 
@@ -128,6 +130,9 @@ _lib.stencil_get_field.argtypes = [_P, _I, _P, _I]
 _lib.stencil_set_fields.argtypes = [_P, _P, _P, _I, ctypes.c_int64]
 _lib.stencil_set_velocity.argtypes = [_P, _P, _I]
 _lib.stencil_get_stats.argtypes = [_P, ctypes.POINTER(stencil_stats)]
+_lib.stencil_checkpoint_size.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.stencil_checkpoint.argtypes = [_P, _P, ctypes.c_uint64, _I]
+_lib.stencil_restore.argtypes = [_P, _P, ctypes.c_uint64, _I]
 _lib.stencil_energy.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_rel_l2.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_double)]
 _lib.stencil_candidates_1d.argtypes = [_I, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I)]
@@ -244,6 +249,31 @@ def stencil_get_stats(plan: int) -> stencil_stats:
     s = stencil_stats()
     _check(_lib.stencil_get_stats(plan, ctypes.byref(s)))
     return s
+
+
+def stencil_checkpoint_size(plan: int) -> int:
+    n = ctypes.c_uint64()
+    _check(_lib.stencil_checkpoint_size(plan, ctypes.byref(n)))
+    return n.value
+
+
+def stencil_checkpoint(plan: int, out=None):
+    """Write the plan's state into ``out`` (a uint8 numpy array or CUDA
+    tensor of at least stencil_checkpoint_size bytes); with no ``out`` a new
+    numpy uint8 array is returned."""
+    if out is None:
+        import numpy as np
+        out = np.empty(stencil_checkpoint_size(plan), dtype=np.uint8)
+    addr, dev = _ptr(out)
+    nbytes = out.nbytes if hasattr(out, "nbytes") else out.numel() * out.element_size()
+    _check(_lib.stencil_checkpoint(plan, addr, nbytes, dev))
+    return out
+
+
+def stencil_restore(plan: int, ckpt) -> None:
+    addr, dev = _ptr(ckpt)
+    nbytes = ckpt.nbytes if hasattr(ckpt, "nbytes") else ckpt.numel() * ckpt.element_size()
+    _check(_lib.stencil_restore(plan, addr, nbytes, dev))
 
 
 def stencil_energy(plan: int) -> float:
@@ -413,8 +443,11 @@ def stencil_version() -> str:
 # ---- convenience -----------------------------------------------------------------
 def make_desc(velocity, dt: float, radius: int = 5, dx: float = 10.0, src=None, f: float = 15.0,
               t0: float = -1.0, amp: float = 1.0, tile=None, graph_steps: int = 0, stream=None,
-              tune_mode: int = STENCIL_TUNE_NONE, storage: int = STENCIL_FP32) -> stencil_desc:
-    """Descriptor for a velocity array of shape (nz, ny, nx); src defaults to the centre."""
+              tune_mode: int = STENCIL_TUNE_NONE, storage: int = STENCIL_FP32,
+              buffers=None) -> stencil_desc:
+    """Descriptor for a velocity array of shape (nz, ny, nx); src defaults to the centre.
+    ``buffers``: three contiguous CUDA float32 tensors (field 0, field 1, kappa)
+    the plan runs on in place of its own allocations."""
     nz, ny, nx = (int(s) for s in velocity.shape)
     d = stencil_desc_init()
     d.nx, d.ny, d.nz = nx, ny, nz
@@ -434,13 +467,21 @@ def make_desc(velocity, dt: float, radius: int = 5, dx: float = 10.0, src=None, 
     addr, dev = _ptr(velocity)
     d.velocity = addr
     d.velocity_on_device = dev
+    if buffers is not None:
+        if len(buffers) != 3:
+            raise ValueError("buffers: field 0, field 1 and kappa")
+        for i, b in enumerate(buffers):
+            a, on_dev = _ptr(b)
+            if not on_dev:
+                raise ValueError("buffers must be CUDA tensors")
+            d.user_buffers[i] = a
     return d
 
 
 EXPORTED = [
     "stencil_desc_init", "stencil_plan", "stencil_destroy", "stencil_step", "stencil_run",
     "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
-    "stencil_get_stats",
+    "stencil_get_stats", "stencil_checkpoint_size", "stencil_checkpoint", "stencil_restore",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
     "stencil_tile_info", "stencil_batch_create", "stencil_batch_run", "stencil_batch_sync",

@@ -303,12 +303,14 @@ void Plan::release()
 {
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
-    for (auto &b : buf)
-        if (b) dev_free(b);
+    if (!user_owned) {
+        for (auto &b : buf)
+            if (b) dev_free(b);
+        if (kappa) dev_free(kappa);
+    }
     for (auto &b : staging)
         if (b) dev_free(b);
     staging[0] = staging[1] = nullptr;
-    if (kappa) dev_free(kappa);
     if (d_scratch) dev_free(d_scratch);
     if (pool && stream) cudaStreamSynchronize(stream);
     if (own_stream && stream) cudaStreamDestroy(stream);
@@ -482,6 +484,19 @@ int validate_desc(const stencil_desc *d)
         return fail(STENCIL_EINVAL, "graph_steps must be 0 or a positive even number");
     if (d->tune_mode < STENCIL_TUNE_NONE || d->tune_mode > STENCIL_TUNE_EXHAUSTIVE)
         return fail(STENCIL_EINVAL, "bad tune_mode");
+    const int n_user = (d->user_buffers[0] != nullptr) + (d->user_buffers[1] != nullptr) +
+                       (d->user_buffers[2] != nullptr);
+    if (n_user) {
+        if (n_user != 3) return fail(STENCIL_EINVAL, "user_buffers: give all three or none");
+        if (d->storage != STENCIL_FP32)
+            return fail(STENCIL_EUNSUPPORTED, "user_buffers need FP32 storage");
+        if (d->nx % 4) return fail(STENCIL_EINVAL, "user_buffers need nx a multiple of 4 (16-byte rows)");
+        for (void *b : d->user_buffers)
+            if (reinterpret_cast<uintptr_t>(b) % 16) return fail(STENCIL_EINVAL, "user_buffers must be 16-byte aligned");
+        if (d->user_buffers[0] == d->user_buffers[1] || d->user_buffers[0] == d->user_buffers[2] ||
+            d->user_buffers[1] == d->user_buffers[2])
+            return fail(STENCIL_EINVAL, "user_buffers must be three different buffers");
+    }
     return STENCIL_OK;
 }
 
@@ -523,7 +538,9 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     p->dt = d->dt;
     p->storage = d->storage;
     p->esize = d->storage == STENCIL_FP32 ? 4 : 2;
-    p->pitch = row_pitch(d->nx, p->esize);
+    p->user_owned = d->user_buffers[0] != nullptr;
+    // caller-owned buffers are dense; the plan's own rows are padded to 128 B
+    p->pitch = p->user_owned ? d->nx : row_pitch(d->nx, p->esize);
     p->field_elems = p->pitch * d->ny * d->nz;
     p->graph_len = d->graph_steps;
     p->tune_mode = d->tune_mode;
@@ -541,12 +558,18 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     }
     const size_t fbytes = (size_t)p->field_elems * p->esize;
     const size_t kbytes = (size_t)p->field_elems * sizeof(float);
-    for (auto &b : p->buf) {
-        e = p->dev_alloc(&b, fbytes);
-        if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(field)"));
+    if (p->user_owned) {
+        p->buf[0] = d->user_buffers[0];
+        p->buf[1] = d->user_buffers[1];
+        p->kappa = static_cast<float *>(d->user_buffers[2]);
+    } else {
+        for (auto &b : p->buf) {
+            e = p->dev_alloc(&b, fbytes);
+            if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(field)"));
+        }
+        e = p->dev_alloc(reinterpret_cast<void **>(&p->kappa), kbytes);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(kappa)"));
     }
-    e = p->dev_alloc(reinterpret_cast<void **>(&p->kappa), kbytes);
-    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(kappa)"));
     // scratch: step counter, error word, v range, reduction partials and
     // result, and (16-bit storage) the per-level per-plane scale and amax tables
     const size_t red_bytes = 256 + sizeof(double) * (2 * RED_BLOCKS + 8);
@@ -565,7 +588,7 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
         p->d_scale = reinterpret_cast<float *>(sc + red_bytes);
         p->d_amax = reinterpret_cast<unsigned *>(sc + red_bytes + 4 * 4 * (size_t)d->nz);
     }
-    p->device_bytes = 2 * (int64_t)fbytes + (int64_t)kbytes + (int64_t)scratch;
+    p->device_bytes = (p->user_owned ? 0 : 2 * (int64_t)fbytes + (int64_t)kbytes) + (int64_t)scratch;
 
     cudaStream_t s = p->stream;
     if ((e = cudaMemsetAsync(p->d_scratch, 0, scratch, s)) != cudaSuccess ||
@@ -800,6 +823,8 @@ int stencil_get_stats(stencil_plan_t h, stencil_stats *s)
     s->selection_ms = p->selection_ms;
     s->n_candidates = p->n_candidates;
     s->tune_mode = p->tune_mode;
+    s->current_buffer = p->cur;
+    s->user_buffers = p->user_owned ? 1 : 0;
     return STENCIL_OK;
 }
 

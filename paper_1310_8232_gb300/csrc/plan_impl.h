@@ -32,6 +32,7 @@ struct Plan {
     int storage = STENCIL_FP32;
     int esize = 4;                        // bytes per wavefield element
     void *buf[2] = {nullptr, nullptr};    // buf[cur] = u^n, buf[cur ^ 1] = u^{n-1}
+    bool user_owned = false;              // buf and kappa belong to the caller (not freed)
     float *kappa = nullptr;
     float *staging[2] = {nullptr, nullptr};   // 16-bit storage: FP32 copies for state transfer
     float *d_scale = nullptr;             // 16-bit storage: [4][nz] per-plane scales by level mod 4
