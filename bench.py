@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--naive", action="store_true", help="time the one-thread-per-point kernel")
     ap.add_argument("--storage", choices=["fp32", "fp16", "bf16"], default="fp32",
                     help="wavefield storage (fp16/bf16: per-plane scaled, FP32 arithmetic)")
+    ap.add_argument("--record", choices=["none", "energy", "traces", "both"], default="none",
+                    help="single: also record the per-step energy and/or a receiver plane at z = 10")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-timesteps", type=int, default=10)
@@ -462,6 +464,9 @@ def main():
     t_plan = time.perf_counter()
     plan = st.stencil_plan(desc)
     plan_ms = 1e3 * (time.perf_counter() - t_plan)
+    if args.record != "none":
+        st.stencil_record_start(plan, receiver_z=10 if args.record in ("traces", "both") else -1,
+                                energy=args.record in ("energy", "both"), capacity=T)
     stats = st.stencil_get_stats(plan)
     t = stats.tile
     etype = {"fp32": "float", "fp16": "__half", "bf16": "__nv_bfloat16"}[args.storage]
@@ -547,7 +552,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
             "data": "synthetic",
-            "config": workload_config(args, {"storage": args.storage,
+            "config": workload_config(args, {"storage": args.storage, "record": args.record,
                 "tile": {"kernel": kernel_tag, "tx": t.tx, "ty": t.ty, "zchunk": t.zchunk},
                 "graph_steps": args.graph, "plan_ms": plan_ms}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -69,7 +69,8 @@ typedef enum {
 } stencil_storage;
 
 typedef enum {
-    STENCIL_KERNEL_AUTO  = 0,  /* library default: the tiled kernel, default tile */
+    STENCIL_KERNEL_AUTO  = 0,  /* library default: the naive kernel for FP32 grids of at most 2^19
+                                  points (latency-bound), else the tiled kernel, default tile */
     STENCIL_KERNEL_NAIVE = 1,  /* one thread per point, neighbours straight from global memory */
     STENCIL_KERNEL_TILED = 2   /* 2.5D blocking: TMA-staged xy tile + halo, z-marching register queue */
 } stencil_kernel;
@@ -216,6 +217,42 @@ STENCIL_API int stencil_set_fields(stencil_plan_t p, const float *u, const float
 STENCIL_API int stencil_set_velocity(stencil_plan_t p, const float *velocity, int32_t on_device);
 
 STENCIL_API int stencil_get_stats(stencil_plan_t p, stencil_stats *s);
+
+/* ---- recording inside the time loop ----------------------------------
+ * Algorithm 1's loop body records the seismic traces ("sismic") and the
+ * energy beside the 3D model step; here the sweep itself writes them after
+ * every step n -> n+1 (single-plan stencil_step / stencil_run, either
+ * kernel; batched and served shots record nothing).
+ *   traces: u^{n+1} on the receiver plane z = receiver_z (receiver_y = -1:
+ *           all ny x nx points; else the nx points of row receiver_y), as
+ *           computed (FP32, before any 16-bit storage rounding);
+ *   energy: E^{n+1/2} = sum_p (u^{n+1}-u^n)^2 / kappa - u^{n+1} Lambda(u^n)
+ *           (conserved by the scheme without a source), FP32 per warp and
+ *           plane, FP64 over warps and blocks in a fixed order.
+ * Record m holds the step from u^{n0+m} to u^{n0+m+1}, n0 = steps_done when
+ * recording started; steps beyond `capacity` records are not recorded. */
+typedef struct {
+    int32_t receiver_z;   /* receiver plane, -1 = no traces */
+    int32_t receiver_y;   /* -1 = the whole plane, else one row */
+    int32_t energy;       /* 1 = record E^{n+1/2} */
+    int32_t capacity;     /* records kept (>= 1) */
+} stencil_record_cfg;
+
+/* receiver_z = receiver_y = -1, energy 0, capacity 0. */
+STENCIL_API void stencil_record_cfg_init(stencil_record_cfg *c);
+/* Start (or restart) recording at the current step: allocates capacity x
+ * (ny or 1) x nx floats of traces and capacity + blocks doubles on the
+ * device.  STENCIL_EINVAL for a receiver outside the grid, capacity < 1 or
+ * nothing to record. */
+STENCIL_API int stencil_record_start(stencil_plan_t p, const stencil_record_cfg *c);
+/* Copy the records made so far (*nrecorded = min(capacity, steps since the
+ * start)): traces into `traces` ([record][ny or 1][nx] floats; device memory
+ * if traces_on_device), energies into host `energy` ([record] doubles);
+ * either may be NULL.  Waits for the plan's stream. */
+STENCIL_API int stencil_record_read(stencil_plan_t p, float *traces, int32_t traces_on_device, double *energy,
+                                    int32_t *nrecorded);
+/* Stop recording and free its buffers (no-op when not recording). */
+STENCIL_API int stencil_record_stop(stencil_plan_t p);
 
 /* ---- checkpoint / restore ---------------------------------------------
  * The time loop's state (Sec. 2, Algorithm 1): the two levels u^n and

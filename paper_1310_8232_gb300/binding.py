@@ -92,6 +92,11 @@ class stencil_stats(ctypes.Structure):
     ]
 
 
+class stencil_record_cfg(ctypes.Structure):
+    _fields_ = [("receiver_z", ctypes.c_int32), ("receiver_y", ctypes.c_int32),
+                ("energy", ctypes.c_int32), ("capacity", ctypes.c_int32)]
+
+
 class shot_server_cfg(ctypes.Structure):
     _fields_ = [
         ("hbm_budget_frac", ctypes.c_double), ("hbm_budget_bytes", ctypes.c_int64),
@@ -130,6 +135,11 @@ _lib.stencil_get_field.argtypes = [_P, _I, _P, _I]
 _lib.stencil_set_fields.argtypes = [_P, _P, _P, _I, ctypes.c_int64]
 _lib.stencil_set_velocity.argtypes = [_P, _P, _I]
 _lib.stencil_get_stats.argtypes = [_P, ctypes.POINTER(stencil_stats)]
+_lib.stencil_record_cfg_init.argtypes = [ctypes.POINTER(stencil_record_cfg)]
+_lib.stencil_record_cfg_init.restype = None
+_lib.stencil_record_start.argtypes = [_P, ctypes.POINTER(stencil_record_cfg)]
+_lib.stencil_record_read.argtypes = [_P, _P, _I, _P, ctypes.POINTER(_I)]
+_lib.stencil_record_stop.argtypes = [_P]
 _lib.stencil_checkpoint_size.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
 _lib.stencil_checkpoint.argtypes = [_P, _P, ctypes.c_uint64, _I]
 _lib.stencil_restore.argtypes = [_P, _P, ctypes.c_uint64, _I]
@@ -249,6 +259,36 @@ def stencil_get_stats(plan: int) -> stencil_stats:
     s = stencil_stats()
     _check(_lib.stencil_get_stats(plan, ctypes.byref(s)))
     return s
+
+
+def stencil_record_cfg_init() -> stencil_record_cfg:
+    c = stencil_record_cfg()
+    _lib.stencil_record_cfg_init(ctypes.byref(c))
+    return c
+
+
+def stencil_record_start(plan: int, receiver_z: int = -1, receiver_y: int = -1, energy: bool = False,
+                         capacity: int = 0) -> None:
+    c = stencil_record_cfg_init()
+    c.receiver_z, c.receiver_y, c.energy, c.capacity = receiver_z, receiver_y, int(bool(energy)), capacity
+    _check(_lib.stencil_record_start(plan, ctypes.byref(c)))
+
+
+def stencil_record_read(plan: int, traces=None, energy=None) -> int:
+    """Copy the records made so far into ``traces`` (float32, numpy or CUDA
+    tensor, [capacity][ny or 1][nx]) and ``energy`` (numpy float64,
+    [capacity]); returns how many records there are."""
+    at, dt_ = _ptr(traces)
+    ae, de = _ptr(energy)
+    if de:
+        raise ValueError("energy must be a host array")
+    n = _I()
+    _check(_lib.stencil_record_read(plan, at or None, dt_, ae or None, ctypes.byref(n)))
+    return n.value
+
+
+def stencil_record_stop(plan: int) -> None:
+    _check(_lib.stencil_record_stop(plan))
 
 
 def stencil_checkpoint_size(plan: int) -> int:
@@ -482,6 +522,7 @@ EXPORTED = [
     "stencil_desc_init", "stencil_plan", "stencil_destroy", "stencil_step", "stencil_run",
     "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
     "stencil_get_stats", "stencil_checkpoint_size", "stencil_checkpoint", "stencil_restore",
+    "stencil_record_cfg_init", "stencil_record_start", "stencil_record_read", "stencil_record_stop",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
     "stencil_tile_info", "stencil_batch_create", "stencil_batch_run", "stencil_batch_sync",

@@ -80,6 +80,16 @@ struct SweepParams {
     const int64_t *step_base;      // device: n of the first step of this launch chunk
     int32_t step_off;              // this launch's offset within the chunk
     int *err;                      // device error word
+    // recording after each step n -> n+1 (single-plan launches; off when
+    // rec_z < 0 and energy_on == 0): record index m = n - rec_n0, m < rec_cap
+    float *rec;                    // receiver traces [rec_cap][rec_y < 0 ? ny : 1][nx] of u^{n+1}
+    double *energy;                // [rec_cap] E^{n+1/2}
+    double *energy_part;           // [grid blocks] per-block partial of the step's energy
+    unsigned *energy_count;        // blocks that have added their partial for the current step
+    int64_t rec_n0;
+    int32_t rec_cap;
+    int32_t rec_z, rec_y;          // receiver plane (-1: none), row (-1: the whole plane)
+    int32_t energy_on;
 };
 
 // A shot of a grouped launch: its tensor maps (by parity of the level),

@@ -12,44 +12,100 @@ namespace stencil {
 // paper's "No-Blocksize" variant (Sec. 3.1): no data staging at all.
 // grid (ceil(nx/128), ny, nz), 128 threads.
 // ---------------------------------------------------------------------------
-template <int R>
+template <int R, bool REC>
 __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     const int z = blockIdx.z;
-    if (x >= p.nx) return;
-    const int64_t q = (int64_t)z * p.plane + (int64_t)y * p.pitch + x;
-    const float *u = static_cast<const float *>(p.u);
-    float *up = static_cast<float *>(p.up);
-    const float c = u[q];
-    float acc = 3.0f * wf<R>(0) * c;
+    if (!REC && x >= p.nx) return;
+    float e = 0.0f;                           // REC: this point's energy term
+    if (x < p.nx) {
+        const int64_t q = (int64_t)z * p.plane + (int64_t)y * p.pitch + x;
+        const float *u = static_cast<const float *>(p.u);
+        float *up = static_cast<float *>(p.up);
+        const float c = u[q];
+        float acc = 3.0f * wf<R>(0) * c;
 #pragma unroll
-    for (int r = 1; r <= R; ++r) {
-        float s = (x - r >= 0) ? u[q - r] : 0.0f;
-        s += (x + r < p.nx) ? u[q + r] : 0.0f;
-        s += (y - r >= 0) ? u[q - r * p.pitch] : 0.0f;
-        s += (y + r < p.ny) ? u[q + r * p.pitch] : 0.0f;
-        s += (z - r >= 0) ? u[q - r * p.plane] : 0.0f;
-        s += (z + r < p.nz) ? u[q + r * p.plane] : 0.0f;
-        acc = fmaf(wf<R>(r), s, acc);
+        for (int r = 1; r <= R; ++r) {
+            float s = (x - r >= 0) ? u[q - r] : 0.0f;
+            s += (x + r < p.nx) ? u[q + r] : 0.0f;
+            s += (y - r >= 0) ? u[q - r * p.pitch] : 0.0f;
+            s += (y + r < p.ny) ? u[q + r * p.pitch] : 0.0f;
+            s += (z - r >= 0) ? u[q - r * p.plane] : 0.0f;
+            s += (z + r < p.nz) ? u[q + r * p.plane] : 0.0f;
+            acc = fmaf(wf<R>(r), s, acc);
+        }
+        const float kap = p.kappa[q];
+        float nxt = fmaf(kap, acc, 2.0f * c - up[q]);
+        if (p.src.on && x == p.src.x && y == p.src.y && z == p.src.z) {
+            const double t = (double)current_step(p) * p.src.dt;
+            nxt += (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
+        }
+        up[q] = nxt;
+        if (REC) {
+            if (p.energy_on) {
+                const float d = nxt - c;
+                e = d * d / kap - nxt * acc;
+            }
+            if (z == p.rec_z && (p.rec_y < 0 || y == p.rec_y)) {
+                const int64_t m = current_step(p) - p.rec_n0;
+                if (m >= 0 && m < p.rec_cap)
+                    p.rec[m * (int64_t)(p.rec_y < 0 ? p.ny : 1) * p.nx + (p.rec_y < 0 ? (int64_t)y * p.nx : 0) + x] =
+                        nxt;
+            }
+        }
     }
-    float nxt = fmaf(p.kappa[q], acc, 2.0f * c - up[q]);
-    if (p.src.on && x == p.src.x && y == p.src.y && z == p.src.z) {
-        const double t = (double)current_step(p) * p.src.dt;
-        nxt += (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
+    if (REC && p.energy_on) {
+        // block partial (FP32 per warp, FP64 over the 4 warps), then the last
+        // block adds every partial in a fixed order with all its threads
+        __shared__ double wsum[4];
+        __shared__ int last;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (double)e;
+        __syncthreads();
+        const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+        if (threadIdx.x == 0) {
+            const unsigned id = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            p.energy_part[id] = ((wsum[0] + wsum[1]) + wsum[2]) + wsum[3];
+            __threadfence();
+            last = atomicAdd(p.energy_count, 1u) == nblk - 1;
+        }
+        __syncthreads();
+        if (last) {
+            __threadfence();
+            __shared__ double tsum[128];
+            double a = 0.0;
+            for (unsigned k = threadIdx.x; k < nblk; k += 128) a += *((volatile const double *)p.energy_part + k);
+            tsum[threadIdx.x] = a;
+            __syncthreads();
+            for (int w = 64; w > 0; w >>= 1) {
+                if (threadIdx.x < w) tsum[threadIdx.x] += tsum[threadIdx.x + w];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
+                const int64_t m = current_step(p) - p.rec_n0;
+                if (m >= 0 && m < p.rec_cap) p.energy[m] = tsum[0];
+                *p.energy_count = 0u;
+            }
+        }
     }
-    up[q] = nxt;
 }
 
 cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)
 {
     if (p.ny > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
     dim3 grid((p.nx + 127) / 128, p.ny, p.nz);
-    if (R == 4)
-        sweep_naive_kernel<4><<<grid, 128, 0, s>>>(p);
+    const bool rec = p.rec_z >= 0 || p.energy_on;
+    if (R == 4 && rec)
+        sweep_naive_kernel<4, true><<<grid, 128, 0, s>>>(p);
+    else if (R == 4)
+        sweep_naive_kernel<4, false><<<grid, 128, 0, s>>>(p);
+    else if (R == 5 && rec)
+        sweep_naive_kernel<5, true><<<grid, 128, 0, s>>>(p);
     else if (R == 5)
-        sweep_naive_kernel<5><<<grid, 128, 0, s>>>(p);
+        sweep_naive_kernel<5, false><<<grid, 128, 0, s>>>(p);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -196,6 +196,15 @@ SweepParams Plan::params(int parity, int step_off) const
     s.amax = d_amax;
     s.growth = growth;
     s.src_bound = src_bound;
+    s.rec = rec;
+    s.energy = rec_energy;
+    s.energy_part = rec_part;
+    s.energy_count = rec_count;
+    s.rec_n0 = rec_n0;
+    s.rec_cap = rec_cap;
+    s.rec_z = rec_mem ? rec_z : -1;
+    s.rec_y = rec_y;
+    s.energy_on = rec_mem ? rec_energy_on : 0;
     return s;
 }
 
@@ -303,6 +312,8 @@ void Plan::release()
 {
     if (stream) cudaStreamSynchronize(stream);
     drop_graphs();
+    if (rec_mem) dev_free(rec_mem);
+    rec_mem = nullptr;
     if (!user_owned) {
         for (auto &b : buf)
             if (b) dev_free(b);
@@ -455,6 +466,14 @@ int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz)
 stencil_tile default_tile(int R, int storage, int nx, int ny, int nz)
 {
     stencil_tile t;
+    if (storage == STENCIL_FP32 && (int64_t)nx * ny * nz <= NAIVE_MAX_POINTS) {
+        // small grids are latency-bound: one pass of one thread per point
+        // beats a z-march whose blocks cannot fill the GPU
+        t.kernel = STENCIL_KERNEL_NAIVE;
+        t.tx = t.ty = 0;
+        t.zchunk = 0;
+        return t;
+    }
     t.kernel = STENCIL_KERNEL_TILED;
     t.tx = 64;
     t.ty = 16;

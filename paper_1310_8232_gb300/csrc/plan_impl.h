@@ -14,6 +14,8 @@ int fail_cuda(cudaError_t e, const char *what);
 double cfl_limit(int R);
 int64_t row_pitch(int nx, int esize);
 int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw, int bh);
+// Grids of at most this many points get the naive kernel by default (FP32).
+constexpr int64_t NAIVE_MAX_POINTS = 1 << 19;
 stencil_tile default_tile(int R, int storage, int nx, int ny, int nz);
 int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz);
 int check_tile(int R, int storage, const stencil_tile &t);
@@ -58,6 +60,13 @@ struct Plan {
     CUtensorMap map_kcore;
     int graph_len = 0;
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+    // recording (receiver traces, per-step energy); off when rec_mem is null
+    void *rec_mem = nullptr;
+    float *rec = nullptr;
+    double *rec_energy = nullptr, *rec_part = nullptr;
+    unsigned *rec_count = nullptr;
+    int64_t rec_n0 = 0;
+    int rec_cap = 0, rec_z = -1, rec_y = -1, rec_energy_on = 0;
     // tile selection results
     int tune_mode = 0;
     double min_time_ms = NAN, actual_time_ms = NAN, full_time_ms = NAN, quality = NAN, selection_ms = NAN;

@@ -120,7 +120,8 @@ struct TiledShape {
     // outputs, plus per-warp maxima (double-buffered by plane parity)
     static constexpr int SIG_BYTES = F32 ? 0 : ((ZMAX + 2 * R) + 2 * ZMAX + 2 * (NT / 32)) * 4;
     static constexpr int BAR_OFF = ((SIG_OFF + SIG_BYTES + 15) / 16) * 16;
-    static constexpr int FLAG_OFF = BAR_OFF + (SU + SA) * 8;
+    static constexpr int EN_OFF = BAR_OFF + (SU + SA) * 8;     // per-warp FP64 energy sums
+    static constexpr int FLAG_OFF = EN_OFF + (NT / 32) * 8;
     static constexpr int SMEM = FLAG_OFF + 16;
     static_assert(TX % 32 == 0 && TX >= 32 && BW <= 256 && BH <= 256, "TMA box limits");
     static_assert(TY % ROWS == 0, "whole thread rows");
@@ -161,7 +162,7 @@ __device__ __forceinline__ float4 scale4(const float4 &v, float s)
 // One block's work: tile (bx, by) of the xy plane, output planes [z0, z1)
 // of one shot, at time level n.  map_* are the shot's tensor maps (kernel
 // parameters or 64-byte aligned global memory).
-template <int R, int TX, int TY, typename E>
+template <int R, int TX, int TY, typename E, bool REC>
 __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUtensorMap *map_up,
                                            const CUtensorMap *map_k, const SweepParams &params, int bx, int by,
                                            int z0, int z1, int64_t n_level, unsigned char *smem)
@@ -184,6 +185,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     const int tid = threadIdx.x;
     const int x0 = bx * TX;
     const int y0 = by * TY;
+    double *en_warp = reinterpret_cast<double *>(smem + S::EN_OFF);   // per-warp energy sums
+    if (REC && tid < S::NT / 32) en_warp[tid] = 0.0;
     if (z0 >= z1) return;                     // uniform over the block
     const int nout = z1 - z0;                 // output planes
     const int nin = nout + 2 * R;             // planes through the ring: z0-R .. z1+R-1
@@ -398,6 +401,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 const int o = z0 + ja;
                 const float inv_out = S::F32 ? 1.0f : 1.0f / sig_out[ja];   // exact: a power of two
                 float omax = 0.0f;
+                float esum = 0.0f;
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) {
                     const float4 c = col[R + h];
@@ -420,6 +424,29 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         else nxt.w += add;
                     }
                     const bool ok = x_ok && gy0 + h < p.ny;
+                    if (REC && p.energy_on && ok) {
+                        // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa - u^{n+1} Lambda(u^n)
+                        const float f[4] = {fA.x, fA.y, fB.x, fB.y};
+                        const float un[4] = {cc.x, cc.y, cc.z, cc.w};
+                        const float u1[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
+                        const float kk[4] = {kap[h].x, kap[h].y, kap[h].z, kap[h].w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const float d = u1[k] - un[k];
+                            if (gx + k < p.nx) esum += d * d / kk[k] - u1[k] * f[k];
+                        }
+                    }
+                    if (REC && o == p.rec_z && ok && (p.rec_y < 0 || p.rec_y == gy0 + h)) {
+                        const int64_t m = n_level - p.rec_n0;
+                        if (m >= 0 && m < p.rec_cap) {
+                            float *t = p.rec + m * (int64_t)(p.rec_y < 0 ? p.ny : 1) * p.nx +
+                                       (p.rec_y < 0 ? (int64_t)(gy0 + h) * p.nx : 0) + gx;
+                            const float u1[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (gx + k < p.nx) t[k] = u1[k];
+                        }
+                    }
                     if constexpr (!S::F32) {
                         if (ok)
                             omax = fmaxf(omax, fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)),
@@ -431,6 +458,12 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 if constexpr (!S::F32) {
                     const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
                     if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
+                }
+                if (REC && p.energy_on) {
+                    // the warp's FP32 sum of this plane, added in FP64 by lane 0
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
+                    if ((tid & 31) == 0) en_warp[tid >> 5] += (double)esum;
                 }
             }
             // slot K held plane i - R - 1, which nothing needs any more
@@ -477,8 +510,9 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     }
 }
 
-// One shot per launch: block (tile, z-chunk) from the grid position.
-template <int R, int TX, int TY, typename E>
+// One shot per launch: block (tile, z-chunk) from the grid position.  REC:
+// the variant that also writes receiver traces and the step's energy.
+template <int R, int TX, int TY, typename E, bool REC = false>
 __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
     sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,
                        const __grid_constant__ CUtensorMap map_k, const SweepParams p)
@@ -488,7 +522,31 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
     const int by = blockIdx.x / p.tiles_x;
     const int z0 = blockIdx.y * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
-    sweep_tile<R, TX, TY, E>(&map_u, &map_up, &map_k, p, bx, by, z0, z1, current_step(p), smem);
+    const int64_t n = current_step(p);
+    sweep_tile<R, TX, TY, E, REC>(&map_u, &map_up, &map_k, p, bx, by, z0, z1, n, smem);
+    if (REC && p.energy_on) {
+        // block partial (warps in order), then the last block to finish adds
+        // all partials in block order: the step's energy, deterministic
+        using S = TiledShape<R, TX, TY, E>;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double *en_warp = reinterpret_cast<const double *>(smem + S::EN_OFF);
+            double b = 0.0;
+            for (int w = 0; w < S::NT / 32; ++w) b += en_warp[w];
+            const unsigned nblk = gridDim.x * gridDim.y;
+            const unsigned id = blockIdx.y * gridDim.x + blockIdx.x;
+            p.energy_part[id] = b;
+            __threadfence();
+            if (atomicAdd(p.energy_count, 1u) == nblk - 1) {
+                __threadfence();
+                double e = 0.0;
+                for (unsigned k = 0; k < nblk; ++k) e += *((volatile const double *)p.energy_part + k);
+                const int64_t m = n - p.rec_n0;
+                if (m >= 0 && m < p.rec_cap) p.energy[m] = e;
+                *p.energy_count = 0u;
+            }
+        }
+    }
 }
 
 // Many shots per launch (one time step of each): block b does work item
@@ -514,7 +572,8 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
         fence_tensormap(&g.core[par ^ 1]);
         fence_tensormap(&g.kcore);
     }
-    sweep_tile<R, TX, TY, E>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n, smem);
+    sweep_tile<R, TX, TY, E, false>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n,
+                                    smem);
 }
 
 }  // namespace stencil

@@ -25,8 +25,11 @@ struct Inst {
             static std::once_flag once;
             static cudaError_t status = cudaSuccess;
             std::call_once(once, [] {
-                status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E>,
+                status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E, false>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+                if (status == cudaSuccess)
+                    status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E, true>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
                 if (status == cudaSuccess)
                     status = cudaFuncSetAttribute(sweep_grouped_kernel<R, TX, TY, E>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -42,7 +45,7 @@ struct Inst {
         } else {
             if (prepare() != cudaSuccess) return 0;
             int n = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tiled_kernel<R, TX, TY, E>, S::NT,
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_tiled_kernel<R, TX, TY, E, false>, S::NT,
                                                               S::SMEM) != cudaSuccess)
                 return 0;
             return n;
@@ -75,7 +78,10 @@ struct Inst {
             q.tiles_x = tiles_x;
             q.zchunk = zc;
             dim3 grid(tiles_x * tiles_y, nzc);
-            sweep_tiled_kernel<R, TX, TY, E><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
+            if (q.rec_z >= 0 || q.energy_on)
+                sweep_tiled_kernel<R, TX, TY, E, true><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
+            else
+                sweep_tiled_kernel<R, TX, TY, E, false><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
             return cudaGetLastError();
         }
     }

@@ -8,6 +8,12 @@ quality (Sec. 3.6) where a selection ran, and the throughput of a full shot
 (--steps time steps) with that tile.  Prints one JSON line per row.
 
     python -m paper_1310_8232_gb300.tile_report [--n 512] [--radius 5] [--steps 200]
+
+With --study nc it re-runs the paper's study of the number of candidates
+(Sec. 3.7, Table 6): MWMB with P = 2, 3, 5, 10 parts per axis, reporting
+nC, the selection cost Total_MWMB(nC), the shot time with the chosen tile
+(Total) and the amortisation rule: a larger candidate set pays off only
+after (Total_MWMB(nC') - Total_MWMB(nC)) / (Total(nC) - Total(nC')) shots.
 """
 from __future__ import annotations
 
@@ -28,6 +34,9 @@ def main(argv=None) -> int:
     ap.add_argument("--streams", type=int, default=4, help="C, concurrent streams ('cores')")
     ap.add_argument("--groups", type=int, default=2, help="N, candidate groups ('nodes')")
     ap.add_argument("--repeat", type=int, default=3, help="timed shots per row")
+    ap.add_argument("--study", choices=["modes", "nc"], default="modes",
+                    help="modes: every selection mode at --parts; nc: MWMB at several P (Sec. 3.7)")
+    ap.add_argument("--parts-list", type=str, default="2,3,5,10", help="--study nc: the values of P")
     args = ap.parse_args(argv)
 
     import torch
@@ -53,10 +62,17 @@ def main(argv=None) -> int:
         ("MAMB", dict(tune_mode=st.STENCIL_TUNE_MAMB)),
         ("exhaustive", dict(tune_mode=st.STENCIL_TUNE_EXHAUSTIVE)),
     ]
+    if args.study == "nc":
+        rows = [("default tile", dict(), args.parts)] + [
+            (f"MWMB P={P}", dict(tune_mode=st.STENCIL_TUNE_MWMB), P)
+            for P in (int(x) for x in args.parts_list.split(","))]
+    else:
+        rows = [(name, kw, args.parts) for name, kw in rows]
     pts = float(n) ** 3 * args.steps
-    for name, kw in rows:
+    results = []
+    for name, kw, parts in rows:
         d = st.make_desc(v, dt, radius=R, dx=workloads.DX, graph_steps=20, stream=stream.cuda_stream, **kw)
-        d.tune.parts, d.tune.iterations = args.parts, args.iterations
+        d.tune.parts, d.tune.iterations = parts, args.iterations
         d.tune.streams, d.tune.groups = args.streams, args.groups
         plan = st.stencil_plan(d)
         try:
@@ -79,16 +95,34 @@ def main(argv=None) -> int:
         def num(x):
             return None if x is None or not math.isfinite(x) else x
 
-        print(json.dumps({
+        row = {
             "row": name, "tile": {"kernel": s.tile.kernel, "tx": s.tile.tx, "ty": s.tile.ty,
                                   "zchunk": s.tile.zchunk},
             "shot_ms": ms, "gpts_per_s": pts / (ms / 1e3) / 1e9,
             "selection_ms": num(s.selection_ms), "candidates": s.n_candidates,
             "min_time_ms": num(s.min_time_ms), "actual_time_ms": num(s.actual_time_ms),
             "quality": num(s.quality), "full_time_ms": num(s.full_time_ms),
-            "config": {"n": n, "radius": R, "steps": args.steps, "P": args.parts, "nI": args.iterations,
+            "config": {"n": n, "radius": R, "steps": args.steps, "P": parts, "nI": args.iterations,
                        "C": args.streams, "N": args.groups},
-        }), flush=True)
+        }
+        results.append(row)
+        print(json.dumps(row), flush=True)
+    if args.study == "nc":
+        # the paper's amortisation rule between consecutive candidate sets,
+        # and against taking the default tile with no selection at all
+        base = results[0]
+        prev = None
+        for r in results[1:]:
+            out = {"row": r["row"] + " amortisation", "candidates": r["candidates"]}
+            for label, other in (("vs_default", base), ("vs_previous_P", prev)):
+                if other is None:
+                    continue
+                extra_ms = (r["selection_ms"] or 0.0) - (other["selection_ms"] or 0.0)
+                gain_ms = other["shot_ms"] - r["shot_ms"]
+                out[label] = {"extra_selection_ms": extra_ms, "gain_per_shot_ms": gain_ms,
+                              "shots_to_break_even": extra_ms / gain_ms if gain_ms > 0 else None}
+            prev = r
+            print(json.dumps(out), flush=True)
     return 0
 
 

@@ -42,7 +42,9 @@ def shot(i, shape, R=5, storage=0):
 
 def alone(env, v, dt, src, steps, R=5, storage=0):
     torch, st = env
-    plan = st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, storage=storage, stream=stream(torch)))
+    # the tiled kernel, as batches and the server run it
+    plan = st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, storage=storage, tile=(2, 64, 16, -1),
+                                        stream=stream(torch)))
     try:
         out = np.empty_like(v)
         st.stencil_run(plan, steps, out)

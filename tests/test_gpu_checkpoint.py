@@ -28,6 +28,7 @@ def make(env, shape=(67, 45, 33), R=5, storage=0, graph=0, seed=3):
     v = workloads.layered_velocity(nx, ny, nz, seed=seed)
     dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
     d = st.make_desc(v, dt, radius=R, src=(nx // 3, ny // 2, nz // 2), storage=storage, graph_steps=graph,
+                     tile=(2, 64, 16, -1),
                      stream=torch.cuda.current_stream().cuda_stream)
     return st.stencil_plan(d), v
 
@@ -113,8 +114,9 @@ def test_user_buffers_run_in_place(env):
     dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
     s = torch.cuda.current_stream().cuda_stream
     bufs = [torch.full((nz, ny, nx), 7.0, device="cuda") for _ in range(3)]
-    own = st.stencil_plan(st.make_desc(v, dt, radius=R, stream=s))
-    mine = st.stencil_plan(st.make_desc(v, dt, radius=R, stream=s, buffers=bufs, graph_steps=4))
+    tile = (2, 64, 16, -1)
+    own = st.stencil_plan(st.make_desc(v, dt, radius=R, stream=s, tile=tile))
+    mine = st.stencil_plan(st.make_desc(v, dt, radius=R, stream=s, buffers=bufs, graph_steps=4, tile=tile))
     try:
         stats = st.stencil_get_stats(mine)
         assert stats.user_buffers == 1 and stats.pitch == nx

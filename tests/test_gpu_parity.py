@@ -31,9 +31,13 @@ def env():
     return torch, st
 
 
-def run_gpu(env, v, dt, R, steps, tile=None, src=None, amp=1.0, u0=None, um1=None, n0=0,
+def run_gpu(env, v, dt, R, steps, tile="default", src=None, amp=1.0, u0=None, um1=None, n0=0,
             graph_steps=0, on_device=True):
+    """tile: "default" = the tiled kernel with the library's default tile
+    shape, None = the library's automatic choice (naive on small grids)."""
     torch, st = env
+    if isinstance(tile, str):
+        tile = DEFAULT_TILED
     vel = torch.from_numpy(v).cuda() if on_device else v
     d = st.make_desc(vel, dt, radius=R, dx=workloads.DX, src=src, amp=amp, tile=tile,
                      graph_steps=graph_steps, stream=cur_stream(torch))
@@ -72,8 +76,11 @@ def tiled(tx, ty, zc):
     return (2, tx, ty, zc)
 
 
+DEFAULT_TILED = tiled(64, 16, -1)
+
+
 @pytest.mark.parametrize("R", [4, 5])
-@pytest.mark.parametrize("tile", [NAIVE, None])
+@pytest.mark.parametrize("tile", [NAIVE, None, "default"])
 @pytest.mark.parametrize("steps", [10, 100])
 def test_single_shot_64_cube(env, R, tile, steps):
     """64^3, constant 2000 m/s, dt = 0.5 CFL, Ricker at the centre."""
@@ -112,7 +119,7 @@ def test_ragged_grid_every_tile(env, R, tile):
 
 @pytest.mark.parametrize("shape", [(1, 1, 40), (5, 5, 5), (9, 11, 1), (33, 1, 17), (4, 70, 3),
                                    (131, 2, 2), (11, 11, 11)])
-@pytest.mark.parametrize("tile", [NAIVE, None, tiled(128, 4, 2)])
+@pytest.mark.parametrize("tile", [NAIVE, None, "default", tiled(128, 4, 2)])
 def test_degenerate_and_tiny_grids(env, shape, tile):
     nx, ny, nz = shape
     R = 5
@@ -177,7 +184,7 @@ def test_split_runs_equal_one_run(env):
     n, R = 40, 4
     v = workloads.layered_velocity(n, n, n, seed=14)
     dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
-    d = st.make_desc(v, dt, radius=R, stream=cur_stream(torch))
+    d = st.make_desc(v, dt, radius=R, tile=DEFAULT_TILED, stream=cur_stream(torch))
     plan = st.stencil_plan(d)
     try:
         st.stencil_step(plan, 13)
@@ -351,3 +358,17 @@ def test_full_size_512_cube_sampled_points(env, R):
         g = got[p[2], p[1], p[0]]
         errs.append(abs(g - ref) / max(1.0, abs(ref)))
     assert max(errs) < 1e-5, max(errs)
+
+
+def test_automatic_kernel_choice_by_grid_size(env):
+    """FP32 grids of at most 2^19 points take the one-pass naive kernel
+    (latency-bound), larger ones and 16-bit storage the tiled kernel."""
+    torch, st = env
+    for shape, storage, kernel in (((64, 64, 64), 0, NAIVE[0]), ((81, 81, 81), 0, 2), ((64, 64, 64), 1, 2)):
+        v = workloads.constant_velocity(*shape, 2000.0)
+        dt = workloads.time_step(oracle.cfl_limit(4), workloads.DX, 2000.0)
+        plan = st.stencil_plan(st.make_desc(v, dt, radius=4, storage=storage, stream=cur_stream(torch)))
+        try:
+            assert st.stencil_get_stats(plan).tile.kernel == kernel, (shape, storage)
+        finally:
+            st.stencil_destroy(plan)

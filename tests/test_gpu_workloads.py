@@ -30,7 +30,7 @@ def env():
 
 
 def alone(st, torch, v, dt, R, steps, src=None):
-    plan = st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, graph_steps=20,
+    plan = st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, graph_steps=20, tile=(2, 64, 16, -1),
                                         stream=torch.cuda.current_stream().cuda_stream))
     try:
         out = np.empty(v.shape, dtype=np.float32)
