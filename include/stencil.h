@@ -69,7 +69,7 @@ typedef enum {
 } stencil_storage;
 
 typedef enum {
-    STENCIL_KERNEL_AUTO  = 0,  /* library default: the naive kernel for FP32 grids of at most 2^19
+    STENCIL_KERNEL_AUTO  = 0,  /* library default: the naive kernel for FP32 grids of at most 2^20
                                   points (latency-bound), else the tiled kernel, default tile */
     STENCIL_KERNEL_NAIVE = 1,  /* one thread per point, neighbours straight from global memory */
     STENCIL_KERNEL_TILED = 2   /* 2.5D blocking: TMA-staged xy tile + halo, z-marching register queue */

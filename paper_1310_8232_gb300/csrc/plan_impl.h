@@ -15,7 +15,7 @@ double cfl_limit(int R);
 int64_t row_pitch(int nx, int esize);
 int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw, int bh);
 // Grids of at most this many points get the naive kernel by default (FP32).
-constexpr int64_t NAIVE_MAX_POINTS = 1 << 19;
+constexpr int64_t NAIVE_MAX_POINTS = 1 << 20;
 stencil_tile default_tile(int R, int storage, int nx, int ny, int nz);
 int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz);
 int check_tile(int R, int storage, const stencil_tile &t);

@@ -279,6 +279,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     int done = 0;                           // planes fully processed (block-uniform)
 
     for (int i0 = 0; i0 < nin; i0 += S::RING) {
+        float2 esum = make_float2(0.f, 0.f);    // REC: energy terms of this group of RING planes
         auto body = [&](auto kc) {
             constexpr int K = decltype(kc)::value;          // slot of plane i
             const int i = i0 + K;
@@ -401,7 +402,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 const int o = z0 + ja;
                 const float inv_out = S::F32 ? 1.0f : 1.0f / sig_out[ja];   // exact: a power of two
                 float omax = 0.0f;
-                float esum = 0.0f;
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) {
                     const float4 c = col[R + h];
@@ -426,15 +426,20 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     const bool ok = x_ok && gy0 + h < p.ny;
                     if (REC && p.energy_on && ok) {
                         // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa - u^{n+1} Lambda(u^n)
-                        const float f[4] = {fA.x, fA.y, fB.x, fB.y};
-                        const float un[4] = {cc.x, cc.y, cc.z, cc.w};
-                        const float u1[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
-                        const float kk[4] = {kap[h].x, kap[h].y, kap[h].z, kap[h].w};
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float d = u1[k] - un[k];
-                            if (gx + k < p.nx) esum += d * d / kk[k] - u1[k] * f[k];
+                        const float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
+                        const float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
+                        const float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
+                        const float2 rA = make_float2(__fdividef(1.0f, kap[h].x), __fdividef(1.0f, kap[h].y));
+                        const float2 rB = make_float2(__fdividef(1.0f, kap[h].z), __fdividef(1.0f, kap[h].w));
+                        float2 eA = __ffma2_rn(__fmul2_rn(dA, dA), rA, __fmul2_rn(neg1, __fmul2_rn(uA, fA)));
+                        float2 eB = __ffma2_rn(__fmul2_rn(dB, dB), rB, __fmul2_rn(neg1, __fmul2_rn(uB, fB)));
+                        if (gx + 4 > p.nx) {              // ragged right edge: points beyond nx
+                            const int nv = p.nx - gx;     // 1 .. 3
+                            if (nv < 2) eA.y = 0.f;
+                            if (nv < 3) eB.x = 0.f;
+                            eB.y = 0.f;
                         }
+                        esum = __fadd2_rn(esum, __fadd2_rn(eA, eB));
                     }
                     if (REC && o == p.rec_z && ok && (p.rec_y < 0 || p.rec_y == gy0 + h)) {
                         const int64_t m = n_level - p.rec_n0;
@@ -459,12 +464,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
                     if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
                 }
-                if (REC && p.energy_on) {
-                    // the warp's FP32 sum of this plane, added in FP64 by lane 0
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) esum += __shfl_xor_sync(0xffffffffu, esum, off);
-                    if ((tid & 31) == 0) en_warp[tid >> 5] += (double)esum;
-                }
+
             }
             // slot K held plane i - R - 1, which nothing needs any more
 #pragma unroll
@@ -494,6 +494,13 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
             }
         };
         Unroll<0, S::RING>::run(body);
+        if (REC && p.energy_on) {
+            // the warp's FP32 sum over these planes, added in FP64 by lane 0
+            float e = esum.x + esum.y;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+            if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
+        }
     }
     if (*abort_flag && tid == 0) {
         // let the copies already issued land before the block's shared

@@ -361,10 +361,11 @@ def test_full_size_512_cube_sampled_points(env, R):
 
 
 def test_automatic_kernel_choice_by_grid_size(env):
-    """FP32 grids of at most 2^19 points take the one-pass naive kernel
+    """FP32 grids of at most 2^20 points take the one-pass naive kernel
     (latency-bound), larger ones and 16-bit storage the tiled kernel."""
     torch, st = env
-    for shape, storage, kernel in (((64, 64, 64), 0, NAIVE[0]), ((81, 81, 81), 0, 2), ((64, 64, 64), 1, 2)):
+    for shape, storage, kernel in (((64, 64, 64), 0, NAIVE[0]), ((128, 64, 128), 0, NAIVE[0]),
+                                   ((102, 102, 102), 0, 2), ((64, 64, 64), 1, 2)):
         v = workloads.constant_velocity(*shape, 2000.0)
         dt = workloads.time_step(oracle.cfl_limit(4), workloads.DX, 2000.0)
         plan = st.stencil_plan(st.make_desc(v, dt, radius=4, storage=storage, stream=cur_stream(torch)))
