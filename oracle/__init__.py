@@ -74,6 +74,11 @@ def _load():
             lib.oracle_sq_diff.argtypes = [ctypes.c_long, ctypes.c_long, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_run_ext.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Ext), ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            lib.oracle_eta.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_long, ctypes.c_long,
+                                                            ctypes.c_long]
+            lib.oracle_eta.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -148,6 +153,68 @@ def run(v, dx: float, dt: float, R: int, steps: int, src=None, f: float = 15.0,
     if rc:
         raise ValueError("oracle_run: bad arguments")
     return u, up
+
+
+class _Ext(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("eta_max", ctypes.c_double),
+                ("inj_z", ctypes.c_int32), ("inj_y", ctypes.c_int32), ("inj", ctypes.c_void_p),
+                ("inj_steps", ctypes.c_int32), ("inj_reverse", ctypes.c_int32), ("inj_scale", ctypes.c_double),
+                ("rec_z", ctypes.c_int32), ("rec_y", ctypes.c_int32), ("rec", ctypes.c_void_p),
+                ("rec_steps", ctypes.c_int32)]
+
+
+def run_ext(v, dx: float, dt: float, R: int, steps: int, src=None, f: float = 15.0,
+            t0: float | None = None, amp: float = 1.0, u0=None, um1=None, n0: int = 0,
+            absorb=(0, 0.0), inject=None, record=None, nthreads: int = 0):
+    """The time loop with an absorbing layer, a plane injection and a plane
+    record (the RTM pieces around the 3D-model step).
+
+    absorb = (width, eta_max); inject = (z, y, data, reverse, scale) with data
+    shaped (steps, rows, nx), rows = ny when y < 0 else 1; record = (z, y).
+    Returns (u, u_prev, traces) with traces shaped (steps, rows, nx) or None.
+    """
+    v = _f64(v)
+    nz, ny, nx = v.shape
+    if src is None:
+        src = (nx // 2, ny // 2, nz // 2)
+    if t0 is None:
+        t0 = 1.0 / f
+    u = np.zeros_like(v) if u0 is None else _f64(u0).copy()
+    up = np.zeros_like(v) if um1 is None else _f64(um1).copy()
+    p = _Problem(nx, ny, nz, R, float(dx), float(dt), v.ctypes.data,
+                 int(src[0]), int(src[1]), int(src[2]), float(f), float(t0), float(amp), int(n0))
+    e = _Ext()
+    e.width, e.eta_max = int(absorb[0]), float(absorb[1])
+    e.inj_z, e.rec_z = -1, -1
+    keep = []
+    if inject is not None:
+        z, y, data, reverse, scale = inject
+        data = _f64(data)
+        keep.append(data)
+        e.inj_z, e.inj_y, e.inj = int(z), int(y), data.ctypes.data
+        e.inj_steps, e.inj_reverse, e.inj_scale = int(data.shape[0]), int(bool(reverse)), float(scale)
+    traces = None
+    if record is not None:
+        z, y = record
+        traces = np.zeros((steps, ny if y < 0 else 1, nx))
+        e.rec_z, e.rec_y, e.rec, e.rec_steps = int(z), int(y), traces.ctypes.data, int(steps)
+    rc = _load().oracle_run_ext(ctypes.byref(p), ctypes.byref(e), int(steps), u.ctypes.data, up.ctypes.data,
+                                int(nthreads))
+    if rc:
+        raise ValueError("oracle_run_ext: bad arguments")
+    return u, up, traces
+
+
+def eta(shape, width: int, eta_max: float) -> np.ndarray:
+    """The absorbing layer's eta at every point, (nz, ny, nx)."""
+    nz, ny, nx = shape
+    out = np.empty(shape)
+    lib = _load()
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                out[k, j, i] = lib.oracle_eta(nx, ny, nz, width, eta_max, i, j, k)
+    return out
 
 
 def energy(v, dx: float, dt: float, R: int, u1, u0) -> float:

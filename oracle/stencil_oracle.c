@@ -296,6 +296,124 @@ int oracle_run(const oracle_problem *p, int steps, int bi, int bj, int bk,
 }
 
 /*
+ * The time loop with the pieces an RTM code adds around the 3D-model step
+ * (the paper names RTM but prints none of them; readings in the design
+ * notes):
+ *   - an absorbing layer: the damped wave equation u_tt + 2 sigma u_t =
+ *     v^2 Laplacian(u), centred in time, i.e. with eta = sigma dt
+ *         u^{n+1} = (2 u^n - (1 - eta) u^{n-1} + kappa Lambda(u^n)) / (1 + eta),
+ *     eta = eta_max ((W - d) / W)^2 within W points of a face (d = distance
+ *     in points to the nearest face, 0 on the face), 0 elsewhere; with
+ *     eta = 0 the expression is the plain update, bit for bit;
+ *   - the point source (as oracle_run);
+ *   - an injection on the plane z = inj_z (one row y = inj_y, or all rows
+ *     when inj_y < 0): u^{n+1} += inj_scale * inj[m] at step m of this call,
+ *     m counted from 0, with inj[inj_steps - 1 - m] instead when
+ *     inj_reverse (time-reversed data, the adjoint source of RTM); steps
+ *     beyond inj_steps inject nothing;
+ *   - a record of u^{n+1} on the plane z = rec_z (row rec_y, or all rows)
+ *     into rec[m] after every step m < rec_steps.
+ * Layout of inj and rec: [step][rows][nx], rows = ny or 1.  Unblocked; the
+ * same OpenMP plane split as oracle_run.
+ */
+typedef struct {
+    int32_t width;          /* absorbing layer in points (0 = none) */
+    double eta_max;
+    int32_t inj_z, inj_y;   /* inj_z < 0: no injection */
+    const double *inj;
+    int32_t inj_steps, inj_reverse;
+    double inj_scale;
+    int32_t rec_z, rec_y;   /* rec_z < 0: no record */
+    double *rec;
+    int32_t rec_steps;
+} oracle_ext;
+
+/* eta at (i,j,k) for a layer of `w` points. */
+double oracle_eta(int nx, int ny, int nz, int w, double eta_max, long i, long j, long k)
+{
+    if (w <= 0) return 0.0;
+    long d = i;
+    if (nx - 1 - i < d) d = nx - 1 - i;
+    if (j < d) d = j;
+    if (ny - 1 - j < d) d = ny - 1 - j;
+    if (k < d) d = k;
+    if (nz - 1 - k < d) d = nz - 1 - k;
+    if (d >= w) return 0.0;
+    const double a = (double)(w - d) / (double)w;
+    return eta_max * a * a;
+}
+
+int oracle_run_ext(const oracle_problem *p, const oracle_ext *e, int steps, double *u, double *u_prev,
+                   int nthreads)
+{
+    grid_t g;
+    if (!p || !e || !u || !u_prev || !p->v || steps < 0) return -1;
+    if (grid_init(&g, p->nx, p->ny, p->nz, p->R)) return -1;
+    const long nx = p->nx, ny = p->ny, nz = p->nz;
+    const long n = nx * ny * nz;
+    if (e->inj_z >= nz || e->inj_y >= ny || e->rec_z >= nz || e->rec_y >= ny) return -1;
+    if ((e->inj_z >= 0 && !e->inj) || (e->rec_z >= 0 && !e->rec)) return -1;
+    double *kappa = (double *)malloc(sizeof(double) * n);
+    double *eta = (double *)malloc(sizeof(double) * n);
+    double *next = (double *)malloc(sizeof(double) * n);
+    if (!kappa || !eta || !next) { free(kappa); free(eta); free(next); return -1; }
+    const double dt2 = p->dt * p->dt, dx2 = p->dx * p->dx;
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                const long q = (k * ny + j) * nx + i;
+                kappa[q] = p->v[q] * p->v[q] * dt2 / dx2;
+                eta[q] = oracle_eta((int)nx, (int)ny, (int)nz, e->width, e->eta_max, i, j, k);
+            }
+    const int has_src = p->amp != 0.0 && p->sx >= 0 && p->sx < nx && p->sy >= 0 &&
+                        p->sy < ny && p->sz >= 0 && p->sz < nz;
+    const long s = has_src ? ((long)p->sz * ny + p->sy) * nx + p->sx : 0;
+#ifdef _OPENMP
+    const int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    const int nt = 1;
+#endif
+    const long inj_rows = e->inj_y < 0 ? ny : 1, rec_rows = e->rec_y < 0 ? ny : 1;
+    for (int step = 0; step < steps; ++step) {
+        #pragma omp parallel for schedule(static) num_threads(nt)
+        for (long k = 0; k < nz; ++k)
+            for (long j = 0; j < ny; ++j)
+                for (long i = 0; i < nx; ++i) {
+                    const long q = (k * ny + j) * nx + i;
+                    next[q] = (2.0 * u[q] - (1.0 - eta[q]) * u_prev[q] + kappa[q] * lap_point(&g, u, i, j, k)) /
+                              (1.0 + eta[q]);
+                }
+        if (has_src) {
+            const double t = (double)(p->n0 + step) * p->dt;
+            next[s] += p->amp * p->v[s] * p->v[s] * dt2 * oracle_ricker(p->f, p->t0, t);
+        }
+        if (e->inj_z >= 0 && step < e->inj_steps) {
+            const long m = e->inj_reverse ? e->inj_steps - 1 - step : step;
+            const double *d = e->inj + m * inj_rows * nx;
+            for (long r = 0; r < inj_rows; ++r) {
+                const long j = e->inj_y < 0 ? r : e->inj_y;
+                for (long i = 0; i < nx; ++i) next[((long)e->inj_z * ny + j) * nx + i] += e->inj_scale * d[r * nx + i];
+            }
+        }
+        if (e->rec_z >= 0 && step < e->rec_steps) {
+            double *d = e->rec + (long)step * rec_rows * nx;
+            for (long r = 0; r < rec_rows; ++r) {
+                const long j = e->rec_y < 0 ? r : e->rec_y;
+                memcpy(d + r * nx, next + ((long)e->rec_z * ny + j) * nx, sizeof(double) * nx);
+            }
+        }
+        /* u_prev <- u, u <- next, through copies (the caller's arrays stay put) */
+        memcpy(u_prev, u, sizeof(double) * n);
+        memcpy(u, next, sizeof(double) * n);
+    }
+    free(kappa);
+    free(eta);
+    free(next);
+    return 0;
+}
+
+/*
  * Discrete energy of the leapfrog scheme between levels n and n+1,
  *   E^{n+1/2} = sum_p [ (u1[p]-u0[p])^2 / kappa[p] - u1[p] * Lambda(u0)[p] ],
  * kappa = v^2 dt^2/dx^2.  This is dx^2 times the scheme's energy
