@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-timesteps", type=int, default=10)
-    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "serve", "rtm"], default="single",
                     help="single: one 512^3 shot; batch: 64 uneven shots in one grouped launch per step "
                          "vs a per-shot loop; serve: Poisson arrivals through the shot server")
     ap.add_argument("--shots", type=int, default=64, help="batch: number of shots")
@@ -407,6 +407,54 @@ def run_serve(args, torch, st, workloads, ranks):
     print(json.dumps(line), flush=True)
 
 
+def run_rtm(args, torch, st, workloads, ranks):
+    """One-shot reverse-time migration: the 8-layer model (seed 1310) on an
+    n^3 grid (--n, default 256 here), --timesteps forward steps (default 600
+    here) with a 20-point absorbing layer, receivers on the plane z = 10,
+    snapshots every 10 steps kept in HBM, then as many backward steps with
+    the reversed traces injected and the imaging condition at every
+    snapshot.  Value = sweep point-updates (2 T n^3) per second of the whole
+    migration (both sweeps, recording, snapshot copies, injection, imaging)."""
+    from paper_1310_8232_gb300 import rtm
+    n = args.n if args.n != 512 else 256
+    T = args.timesteps if args.timesteps != 200 else 600
+    R, k = args.radius, 10
+    v = torch.from_numpy(workloads.layered_velocity(n, n, n, seed=1310)).cuda()
+    dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(v.max()))
+    src = (n // 2, n // 2, 12)
+
+    def once():
+        return rtm.migrate(torch, v, dt, T, src, 10, k, radius=R, dx=workloads.DX, absorb=(20, 0.2),
+                           graph_steps=10)
+
+    for _ in range(max(1, args.warmup)):
+        once()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(ranks.env.local) as clk:
+        for _ in range(args.steps):
+            ranks.barrier()
+            t0 = time.perf_counter()
+            image, _ = once()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * ranks.max(sum(times) / len(times))
+    pts = 2.0 * T * float(n) ** 3
+    if not ranks.is_root:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": ranks.env.world * pts / (ms / 1e3) / 1e9, "unit": METRIC,
+        "n_gpus": ranks.env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"one-shot RTM, {n}^3 8-layer model (seed 1310), R={R}, {T} forward + {T} backward "
+                               "steps, 20-point absorbing layer, receiver plane z=10, snapshots every 10 steps "
+                               "in HBM, zero-lag cross-correlation image", "n": n, "timesteps": T,
+                   "snapshots": T // k, "parallelism": "replicas (one shot per GPU)"},
+        "timing": "host wall clock around the whole migration with device synchronisation",
+        "clocks": clk.summary(),
+    }), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -424,7 +472,7 @@ def main():
         __graft_entry__.build_library()
         from paper_1310_8232_gb300 import binding as st
         from paper_1310_8232_gb300 import workloads
-        fn = run_batch if args.workload == "batch" else run_serve
+        fn = {"batch": run_batch, "serve": run_serve, "rtm": run_rtm}[args.workload]
         fn(args, torch, st, workloads, ranks)
         ranks.close()
         return

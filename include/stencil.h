@@ -139,6 +139,14 @@ typedef struct {
                                     u^{-1} = 0) and writes kappa into [2]; u^n is then in
                                     user_buffers[stats.current_buffer].  They stay the caller's
                                     and must outlive the plan; the shot server does not take them. */
+    int32_t absorb_width;        /* absorbing layer: points from each face (0 = none, the plain
+                                    ghost-zero boundary); single plans only (batches and the shot
+                                    server refuse it with STENCIL_EUNSUPPORTED) */
+    double  absorb_eta;          /* eta = sigma dt at the face, >= 0: the layer solves the damped
+                                    equation u_tt + 2 sigma u_t = v^2 Laplacian(u), centred in time,
+                                    u^{n+1} = (2u^n - (1-eta) u^{n-1} + kappa Lambda(u^n)) / (1+eta),
+                                    eta = absorb_eta ((W-d)/W)^2 at distance d < W from the nearest
+                                    face (the paper names RTM but not its boundary treatment) */
 } stencil_desc;
 
 /* Plan state, results of tuning and the device layout. */
@@ -253,6 +261,34 @@ STENCIL_API int stencil_record_read(stencil_plan_t p, float *traces, int32_t tra
                                     int32_t *nrecorded);
 /* Stop recording and free its buffers (no-op when not recording). */
 STENCIL_API int stencil_record_stop(stencil_plan_t p);
+
+/* ---- RTM pieces: plane injection and the imaging condition ------------
+ * Reverse-time migration (the application the paper's kernel serves, Sec. 2)
+ * propagates the recorded traces backwards in time from the receiver plane
+ * and correlates that wavefield with the source wavefield.  Injection: after
+ * every step n -> n+1, u^{n+1} += scale * data[m] on the plane z (row y, or
+ * all rows when y < 0), m = n - n0 (n0 = steps_done at the start), or
+ * data[steps - 1 - m] when reverse (time-reversed traces); steps outside
+ * [0, steps) inject nothing.  data: device memory, [steps][ny or 1][nx]
+ * FP32, owned by the caller, read during the plan's steps until
+ * stencil_inject_stop.  FP32 storage only (STENCIL_EUNSUPPORTED otherwise:
+ * the 16-bit scale bound does not cover injected values). */
+typedef struct {
+    int32_t z, y;
+    const float *data;
+    int32_t steps;
+    int32_t reverse;
+    float   scale;
+} stencil_inject_cfg;
+
+STENCIL_API int stencil_inject_start(stencil_plan_t p, const stencil_inject_cfg *c);
+STENCIL_API int stencil_inject_stop(stencil_plan_t p);
+
+/* Zero-lag cross-correlation imaging condition: image[p] += scale *
+ * snapshot[p] * u^n[p] for every grid point, u^n the plan's current level.
+ * snapshot and image: device memory, dense nx*ny*nz FP32.  Enqueued on the
+ * plan's stream (returns at once).  16 B per point of HBM traffic. */
+STENCIL_API int stencil_image_accumulate(stencil_plan_t p, const float *snapshot, float *image, float scale);
 
 /* ---- checkpoint / restore ---------------------------------------------
  * The time loop's state (Sec. 2, Algorithm 1): the two levels u^n and

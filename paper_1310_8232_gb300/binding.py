@@ -76,6 +76,7 @@ class stencil_desc(ctypes.Structure):
         ("tile", stencil_tile), ("tune", stencil_tune_params),
         ("cuda_stream", ctypes.c_void_p), ("graph_steps", ctypes.c_int32),
         ("user_buffers", ctypes.c_void_p * 3),
+        ("absorb_width", ctypes.c_int32), ("absorb_eta", ctypes.c_double),
     ]
 
 
@@ -95,6 +96,11 @@ class stencil_stats(ctypes.Structure):
 class stencil_record_cfg(ctypes.Structure):
     _fields_ = [("receiver_z", ctypes.c_int32), ("receiver_y", ctypes.c_int32),
                 ("energy", ctypes.c_int32), ("capacity", ctypes.c_int32)]
+
+
+class stencil_inject_cfg(ctypes.Structure):
+    _fields_ = [("z", ctypes.c_int32), ("y", ctypes.c_int32), ("data", ctypes.c_void_p),
+                ("steps", ctypes.c_int32), ("reverse", ctypes.c_int32), ("scale", ctypes.c_float)]
 
 
 class shot_server_cfg(ctypes.Structure):
@@ -140,6 +146,9 @@ _lib.stencil_record_cfg_init.restype = None
 _lib.stencil_record_start.argtypes = [_P, ctypes.POINTER(stencil_record_cfg)]
 _lib.stencil_record_read.argtypes = [_P, _P, _I, _P, ctypes.POINTER(_I)]
 _lib.stencil_record_stop.argtypes = [_P]
+_lib.stencil_inject_start.argtypes = [_P, ctypes.POINTER(stencil_inject_cfg)]
+_lib.stencil_inject_stop.argtypes = [_P]
+_lib.stencil_image_accumulate.argtypes = [_P, _P, _P, ctypes.c_float]
 _lib.stencil_checkpoint_size.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
 _lib.stencil_checkpoint.argtypes = [_P, _P, ctypes.c_uint64, _I]
 _lib.stencil_restore.argtypes = [_P, _P, ctypes.c_uint64, _I]
@@ -289,6 +298,29 @@ def stencil_record_read(plan: int, traces=None, energy=None) -> int:
 
 def stencil_record_stop(plan: int) -> None:
     _check(_lib.stencil_record_stop(plan))
+
+
+def stencil_inject_start(plan: int, z: int, data, y: int = -1, reverse: bool = False, scale: float = 1.0) -> None:
+    """Inject ``data`` (CUDA float32 tensor, [steps][ny or 1][nx]) on plane z
+    after every step from now on (reversed in time when ``reverse``)."""
+    addr, dev = _ptr(data)
+    if not dev:
+        raise ValueError("injection data must be a CUDA tensor")
+    c = stencil_inject_cfg(int(z), int(y), addr, int(data.shape[0]), int(bool(reverse)), float(scale))
+    _check(_lib.stencil_inject_start(plan, ctypes.byref(c)))
+
+
+def stencil_inject_stop(plan: int) -> None:
+    _check(_lib.stencil_inject_stop(plan))
+
+
+def stencil_image_accumulate(plan: int, snapshot, image, scale: float = 1.0) -> None:
+    """image += scale * snapshot * u^n (CUDA float32 tensors of the grid's shape)."""
+    a, da = _ptr(snapshot)
+    b, db = _ptr(image)
+    if not (da and db):
+        raise ValueError("snapshot and image must be CUDA tensors")
+    _check(_lib.stencil_image_accumulate(plan, a, b, float(scale)))
 
 
 def stencil_checkpoint_size(plan: int) -> int:
@@ -484,7 +516,7 @@ def stencil_version() -> str:
 def make_desc(velocity, dt: float, radius: int = 5, dx: float = 10.0, src=None, f: float = 15.0,
               t0: float = -1.0, amp: float = 1.0, tile=None, graph_steps: int = 0, stream=None,
               tune_mode: int = STENCIL_TUNE_NONE, storage: int = STENCIL_FP32,
-              buffers=None) -> stencil_desc:
+              buffers=None, absorb=(0, 0.0)) -> stencil_desc:
     """Descriptor for a velocity array of shape (nz, ny, nx); src defaults to the centre.
     ``buffers``: three contiguous CUDA float32 tensors (field 0, field 1, kappa)
     the plan runs on in place of its own allocations."""
@@ -502,6 +534,7 @@ def make_desc(velocity, dt: float, radius: int = 5, dx: float = 10.0, src=None, 
         kernel, tx, ty, zc = tile
         d.tile = stencil_tile(kernel, tx, ty, zc)
     d.graph_steps = graph_steps
+    d.absorb_width, d.absorb_eta = int(absorb[0]), float(absorb[1])
     if stream is not None:
         d.cuda_stream = int(stream)
     addr, dev = _ptr(velocity)
@@ -523,6 +556,7 @@ EXPORTED = [
     "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
     "stencil_get_stats", "stencil_checkpoint_size", "stencil_checkpoint", "stencil_restore",
     "stencil_record_cfg_init", "stencil_record_start", "stencil_record_read", "stencil_record_stop",
+    "stencil_inject_start", "stencil_inject_stop", "stencil_image_accumulate",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
     "stencil_tile_info", "stencil_batch_create", "stencil_batch_run", "stencil_batch_sync",

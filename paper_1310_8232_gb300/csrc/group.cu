@@ -81,8 +81,10 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
         g.kcore = p->map_kcore;
         g.prm = p->params(0, 0);
         g.prm.zchunk = zchunk;
-        g.prm.rec_z = -1;           // grouped launches record nothing
+        g.prm.rec_z = -1;           // grouped launches run the plain sweep
         g.prm.energy_on = 0;
+        g.prm.inj_z = -1;
+        g.prm.absorb_w = 0;
         g.buf[0] = p->buf[0];
         g.buf[1] = p->buf[1];
         g.n_end = n_end[i];
@@ -223,6 +225,9 @@ int stencil_batch_create(const stencil_desc *descs, int32_t n, int32_t graph_ste
         b->own_stream = true;
     }
     const int R = descs[0].radius, storage = descs[0].storage;
+    for (int i = 0; i < n; ++i)
+        if (descs[i].absorb_width > 0 && descs[i].absorb_eta > 0.0)
+            return bail(fail(STENCIL_EUNSUPPORTED, "batches run the plain sweep: no absorbing layer"));
     stencil_tile tile = descs[0].tile;
     if (tile.kernel == STENCIL_KERNEL_AUTO) {
         tile.kernel = STENCIL_KERNEL_TILED;

@@ -11,6 +11,8 @@ namespace stencil {
 
 // ---- K0: one thread per point (the GPU "No-Blocksize" analogue) ----
 cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s);
+cudaError_t launch_image_accumulate(const float *s, const float *u, float *img, int nx, int ny, int nz,
+                                    int64_t pitch, float scale, cudaStream_t st);
 
 // ---- K4: kappa = v^2 dt^2/dx^2 in place over a pitched copy of v; v range ----
 // vmax_bits / n_bad are device scalars (uint32 bit pattern of the max, count

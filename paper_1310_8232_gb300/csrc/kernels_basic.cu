@@ -1,6 +1,8 @@
 // K0 (naive sweep), K4 (coefficient init + velocity range), K5 (FP64
-// validation reductions) and the step-counter kernel.
+// validation reductions), the step-counter kernel and the imaging condition.
 #include <math.h>
+
+#include <algorithm>
 
 #include "internal.h"
 
@@ -37,10 +39,24 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
             acc = fmaf(wf<R>(r), s, acc);
         }
         const float kap = p.kappa[q];
-        float nxt = fmaf(kap, acc, 2.0f * c - up[q]);
+        float nxt;
+        float eta = 0.0f;
+        if (REC && p.absorb_w > 0)
+            eta = absorb_eta(p, min(min(min(x, p.nx - 1 - x), min(y, p.ny - 1 - y)), min(z, p.nz - 1 - z)));
+        if (REC && eta > 0.0f)     // absorbing layer: (2u - (1 - eta) u^{n-1} + kappa Lambda) / (1 + eta)
+            nxt = fmaf(kap, acc, fmaf(eta - 1.0f, up[q], 2.0f * c)) * (1.0f / (1.0f + eta));
+        else
+            nxt = fmaf(kap, acc, 2.0f * c - up[q]);
         if (p.src.on && x == p.src.x && y == p.src.y && z == p.src.z) {
             const double t = (double)current_step(p) * p.src.dt;
             nxt += (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
+        }
+        if (REC && z == p.inj_z && (p.inj_y < 0 || y == p.inj_y)) {
+            const int64_t m = current_step(p) - p.inj_n0;
+            const int64_t idx = p.inj_reverse ? p.inj_steps - 1 - m : m;
+            if (m >= 0 && idx >= 0 && idx < p.inj_steps)
+                nxt += p.inj_scale * p.inj[idx * (int64_t)(p.inj_y < 0 ? p.ny : 1) * p.nx +
+                                           (p.inj_y < 0 ? (int64_t)y * p.nx : 0) + x];
         }
         up[q] = nxt;
         if (REC) {
@@ -97,7 +113,7 @@ cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)
 {
     if (p.ny > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
     dim3 grid((p.nx + 127) / 128, p.ny, p.nz);
-    const bool rec = p.rec_z >= 0 || p.energy_on;
+    const bool rec = sweep_extended(p);
     if (R == 4 && rec)
         sweep_naive_kernel<4, true><<<grid, 128, 0, s>>>(p);
     else if (R == 4)
@@ -302,6 +318,38 @@ cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStrea
 cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s)
 {
     advance_kernel<<<1, 1, 0, s>>>(n, k);
+    return cudaGetLastError();
+}
+
+}  // namespace stencil
+
+namespace stencil {
+
+// ---------------------------------------------------------------------------
+// Zero-lag cross-correlation imaging condition: img += scale * s * u over a
+// dense (s, img) and a pitched u grid; 4 points per thread where the row
+// allows it.  HBM-bound: 16 B per point.
+// ---------------------------------------------------------------------------
+__global__ void image_accumulate_kernel(const float *s, const float *u, float *img, int nx, int64_t rows,
+                                        int64_t pitch, float scale)
+{
+    const int64_t total = rows * nx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / nx;
+        const int x = (int)(i - row * nx);
+        img[i] = fmaf(scale * s[i], u[row * pitch + x], img[i]);
+    }
+}
+
+cudaError_t launch_image_accumulate(const float *s, const float *u, float *img, int nx, int ny, int nz,
+                                    int64_t pitch, float scale, cudaStream_t st)
+{
+    const int64_t rows = (int64_t)ny * nz;
+    const int64_t total = rows * nx;
+    const int64_t want = (total + 255) / 256;
+    const int blocks = (int)std::min<int64_t>(want, 152 * 16);
+    image_accumulate_kernel<<<blocks, 256, 0, st>>>(s, u, img, nx, rows, pitch, scale);
     return cudaGetLastError();
 }
 

@@ -205,6 +205,15 @@ SweepParams Plan::params(int parity, int step_off) const
     s.rec_z = rec_mem ? rec_z : -1;
     s.rec_y = rec_y;
     s.energy_on = rec_mem ? rec_energy_on : 0;
+    s.inj = inj;
+    s.inj_n0 = inj_n0;
+    s.inj_steps = inj_steps;
+    s.inj_reverse = inj_reverse;
+    s.inj_z = inj ? inj_z : -1;
+    s.inj_y = inj_y;
+    s.inj_scale = inj_scale;
+    s.absorb_w = absorb_w;
+    s.absorb_eta = absorb_eta;
     return s;
 }
 
@@ -503,6 +512,8 @@ int validate_desc(const stencil_desc *d)
         return fail(STENCIL_EINVAL, "graph_steps must be 0 or a positive even number");
     if (d->tune_mode < STENCIL_TUNE_NONE || d->tune_mode > STENCIL_TUNE_EXHAUSTIVE)
         return fail(STENCIL_EINVAL, "bad tune_mode");
+    if (d->absorb_width < 0 || !(d->absorb_eta >= 0.0) || !std::isfinite(d->absorb_eta))
+        return fail(STENCIL_EINVAL, "absorb_width must be >= 0 and absorb_eta finite and >= 0");
     const int n_user = (d->user_buffers[0] != nullptr) + (d->user_buffers[1] != nullptr) +
                        (d->user_buffers[2] != nullptr);
     if (n_user) {
@@ -563,6 +574,8 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     p->field_elems = p->pitch * d->ny * d->nz;
     p->graph_len = d->graph_steps;
     p->tune_mode = d->tune_mode;
+    p->absorb_w = d->absorb_eta > 0.0 ? d->absorb_width : 0;
+    p->absorb_eta = (float)d->absorb_eta;
     auto bail = [&](int code) {
         p->release();
         delete p;

@@ -67,6 +67,13 @@ struct Plan {
     unsigned *rec_count = nullptr;
     int64_t rec_n0 = 0;
     int rec_cap = 0, rec_z = -1, rec_y = -1, rec_energy_on = 0;
+    // absorbing layer and plane injection
+    int absorb_w = 0;
+    float absorb_eta = 0.0f;
+    const float *inj = nullptr;
+    int64_t inj_n0 = 0;
+    int inj_steps = 0, inj_reverse = 0, inj_z = -1, inj_y = -1;
+    float inj_scale = 0.0f;
     // tile selection results
     int tune_mode = 0;
     double min_time_ms = NAN, actual_time_ms = NAN, full_time_ms = NAN, quality = NAN, selection_ms = NAN;
