@@ -58,6 +58,8 @@ def parse_args():
                     help="wavefield storage (fp16/bf16: per-plane scaled, FP32 arithmetic)")
     ap.add_argument("--record", choices=["none", "energy", "traces", "both"], default="none",
                     help="single: also record the per-step energy and/or a receiver plane at z = 10")
+    ap.add_argument("--absorb", type=int, default=0,
+                    help="single: absorbing layer of this many points on every face (eta_max 0.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-timesteps", type=int, default=10)
@@ -508,7 +510,8 @@ def main():
     else:
         tile = None
     desc = st.make_desc(dv, dt, radius=R, dx=workloads.DX, tile=tile, graph_steps=args.graph,
-                        stream=stream.cuda_stream, storage=STORAGE_ID[args.storage])
+                        stream=stream.cuda_stream, storage=STORAGE_ID[args.storage],
+                        absorb=(args.absorb, 0.2 if args.absorb else 0.0))
     t_plan = time.perf_counter()
     plan = st.stencil_plan(desc)
     plan_ms = 1e3 * (time.perf_counter() - t_plan)
@@ -600,7 +603,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "fp32" else f"f32 arithmetic, {args.storage} storage",
             "data": "synthetic",
-            "config": workload_config(args, {"storage": args.storage, "record": args.record,
+            "config": workload_config(args, {"storage": args.storage, "record": args.record, "absorb": args.absorb,
                 "tile": {"kernel": kernel_tag, "tx": t.tx, "ty": t.ty, "zchunk": t.zchunk},
                 "graph_steps": args.graph, "plan_ms": plan_ms}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

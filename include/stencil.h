@@ -140,8 +140,10 @@ typedef struct {
                                     user_buffers[stats.current_buffer].  They stay the caller's
                                     and must outlive the plan; the shot server does not take them. */
     int32_t absorb_width;        /* absorbing layer: points from each face (0 = none, the plain
-                                    ghost-zero boundary); single plans only (batches and the shot
-                                    server refuse it with STENCIL_EUNSUPPORTED) */
+                                    ghost-zero boundary); FP32 storage and single plans only
+                                    (16-bit storage, batches and the shot server refuse it with
+                                    STENCIL_EUNSUPPORTED); run as a save of u^{n-1} on the layer
+                                    before each sweep and a damping pass after it */
     double  absorb_eta;          /* eta = sigma dt at the face, >= 0: the layer solves the damped
                                     equation u_tt + 2 sigma u_t = v^2 Laplacian(u), centred in time,
                                     u^{n+1} = (2u^n - (1-eta) u^{n-1} + kappa Lambda(u^n)) / (1+eta),
@@ -233,10 +235,13 @@ STENCIL_API int stencil_get_stats(stencil_plan_t p, stencil_stats *s);
  * kernel; batched and served shots record nothing).
  *   traces: u^{n+1} on the receiver plane z = receiver_z (receiver_y = -1:
  *           all ny x nx points; else the nx points of row receiver_y), as
- *           computed (FP32, before any 16-bit storage rounding);
+ *           stored (exactly what stencil_get_field returns), copied by a
+ *           small kernel after each step;
  *   energy: E^{n+1/2} = sum_p (u^{n+1}-u^n)^2 / kappa - u^{n+1} Lambda(u^n)
- *           (conserved by the scheme without a source), FP32 per warp and
- *           plane, FP64 over warps and blocks in a fixed order.
+ *           (conserved by the scheme without a source), summed inside the
+ *           sweep: FP32 per warp over a few planes, FP64 over warps and
+ *           blocks in a fixed order; not with an absorbing layer or an
+ *           injection (STENCIL_EUNSUPPORTED).
  * Record m holds the step from u^{n0+m} to u^{n0+m+1}, n0 = steps_done when
  * recording started; steps beyond `capacity` records are not recorded. */
 typedef struct {
@@ -272,7 +277,8 @@ STENCIL_API int stencil_record_stop(stencil_plan_t p);
  * [0, steps) inject nothing.  data: device memory, [steps][ny or 1][nx]
  * FP32, owned by the caller, read during the plan's steps until
  * stencil_inject_stop.  FP32 storage only (STENCIL_EUNSUPPORTED otherwise:
- * the 16-bit scale bound does not cover injected values). */
+ * the 16-bit scale bound does not cover injected values).  Order within a
+ * step: sweep, absorbing layer, point source, injection, record. */
 typedef struct {
     int32_t z, y;
     const float *data;

@@ -80,42 +80,15 @@ struct SweepParams {
     const int64_t *step_base;      // device: n of the first step of this launch chunk
     int32_t step_off;              // this launch's offset within the chunk
     int *err;                      // device error word
-    // recording after each step n -> n+1 (single-plan launches; off when
-    // rec_z < 0 and energy_on == 0): record index m = n - rec_n0, m < rec_cap
-    float *rec;                    // receiver traces [rec_cap][rec_y < 0 ? ny : 1][nx] of u^{n+1}
+    // energy of each step n -> n+1 (single-plan launches; off when
+    // energy_on == 0): record index m = n - rec_n0, m < rec_cap
     double *energy;                // [rec_cap] E^{n+1/2}
     double *energy_part;           // [grid blocks] per-block partial of the step's energy
     unsigned *energy_count;        // blocks that have added their partial for the current step
     int64_t rec_n0;
     int32_t rec_cap;
-    int32_t rec_z, rec_y;          // receiver plane (-1: none), row (-1: the whole plane)
     int32_t energy_on;
-    // absorbing layer (damped wave equation, eta = eta_max ((W - d) / W)^2
-    // within W points of a face) and plane injection u^{n+1} += inj_scale *
-    // inj[m] on z = inj_z, m = n - inj_n0 (inj_steps - 1 - m when reversed)
-    const float *inj;              // [inj_steps][inj_y < 0 ? ny : 1][nx]
-    int64_t inj_n0;
-    int32_t inj_steps, inj_reverse;
-    int32_t inj_z, inj_y;          // inj_z < 0: no injection
-    float inj_scale;
-    int32_t absorb_w;              // 0: no absorbing layer
-    float absorb_eta;
 };
-
-// true when a launch needs the extended sweep (recording, absorbing layer,
-// injection)
-__host__ __device__ inline bool sweep_extended(const SweepParams &p)
-{
-    return p.rec_z >= 0 || p.energy_on || p.absorb_w > 0 || p.inj_z >= 0;
-}
-
-// eta of the absorbing layer at distance d (points) from the nearest face
-__device__ __forceinline__ float absorb_eta(const SweepParams &p, int d)
-{
-    if (d >= p.absorb_w) return 0.0f;
-    const float a = (float)(p.absorb_w - d) / (float)p.absorb_w;
-    return p.absorb_eta * a * a;
-}
 
 // A shot of a grouped launch: its tensor maps (by parity of the level),
 // buffers and parameters, in 64-byte aligned device memory.

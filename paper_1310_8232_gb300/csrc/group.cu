@@ -81,10 +81,7 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
         g.kcore = p->map_kcore;
         g.prm = p->params(0, 0);
         g.prm.zchunk = zchunk;
-        g.prm.rec_z = -1;           // grouped launches run the plain sweep
-        g.prm.energy_on = 0;
-        g.prm.inj_z = -1;
-        g.prm.absorb_w = 0;
+        g.prm.energy_on = 0;        // grouped launches run the plain sweep
         g.buf[0] = p->buf[0];
         g.buf[1] = p->buf[1];
         g.n_end = n_end[i];

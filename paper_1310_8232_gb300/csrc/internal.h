@@ -33,6 +33,35 @@ cudaError_t launch_sqdiff(const float *a, const double *b, int nx, int ny, int n
 // n += k on the device (step counter between launch chunks)
 cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s);
 
+// ---- per-step operations around the plain sweep (plane_ops.cu) ----
+struct StepOps {
+    int32_t nx, ny, nz;
+    int64_t pitch, plane;
+    const int64_t *step_base;       // n of this step = *step_base + step_off
+    int32_t step_off;
+    // absorbing layer: u^{n-1} of the layer's points saved before the sweep
+    int32_t absorb_w;               // 0: none
+    float absorb_eta;
+    int64_t shell_points;
+    float *save;
+    Source src;                     // added after the layer when absorb_w > 0
+    // plane injection (FP32 storage)
+    const float *inj;
+    int64_t inj_n0;
+    int32_t inj_steps, inj_reverse, inj_z, inj_y;
+    float inj_scale;
+    // plane record
+    float *rec;
+    const float *scale;             // 16-bit storage: [4][nz] per-plane scales; null for FP32
+    int64_t rec_n0;
+    int32_t rec_cap, rec_z, rec_y;
+};
+// points of the layer shell within w of a face
+int64_t shell_points(int nx, int ny, int nz, int w);
+// before the sweep (up = u^{n-1}) / after it (up = u^{n+1})
+cudaError_t launch_step_pre(const StepOps &o, void *up, cudaStream_t s);
+cudaError_t launch_step_post(const StepOps &o, void *up, int storage, cudaStream_t s);
+
 // ---- K1 / K2: 2.5D tiled sweep (TMA-staged xy tile + halo, z register ring) ----
 struct TiledMaps {
     CUtensorMap u_halo;   // u^n, box (tx + 2 hx) x (ty + 2R) x 1

@@ -39,37 +39,15 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
             acc = fmaf(wf<R>(r), s, acc);
         }
         const float kap = p.kappa[q];
-        float nxt;
-        float eta = 0.0f;
-        if (REC && p.absorb_w > 0)
-            eta = absorb_eta(p, min(min(min(x, p.nx - 1 - x), min(y, p.ny - 1 - y)), min(z, p.nz - 1 - z)));
-        if (REC && eta > 0.0f)     // absorbing layer: (2u - (1 - eta) u^{n-1} + kappa Lambda) / (1 + eta)
-            nxt = fmaf(kap, acc, fmaf(eta - 1.0f, up[q], 2.0f * c)) * (1.0f / (1.0f + eta));
-        else
-            nxt = fmaf(kap, acc, 2.0f * c - up[q]);
+        float nxt = fmaf(kap, acc, 2.0f * c - up[q]);
         if (p.src.on && x == p.src.x && y == p.src.y && z == p.src.z) {
             const double t = (double)current_step(p) * p.src.dt;
             nxt += (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
         }
-        if (REC && z == p.inj_z && (p.inj_y < 0 || y == p.inj_y)) {
-            const int64_t m = current_step(p) - p.inj_n0;
-            const int64_t idx = p.inj_reverse ? p.inj_steps - 1 - m : m;
-            if (m >= 0 && idx >= 0 && idx < p.inj_steps)
-                nxt += p.inj_scale * p.inj[idx * (int64_t)(p.inj_y < 0 ? p.ny : 1) * p.nx +
-                                           (p.inj_y < 0 ? (int64_t)y * p.nx : 0) + x];
-        }
         up[q] = nxt;
-        if (REC) {
-            if (p.energy_on) {
-                const float d = nxt - c;
-                e = d * d / kap - nxt * acc;
-            }
-            if (z == p.rec_z && (p.rec_y < 0 || y == p.rec_y)) {
-                const int64_t m = current_step(p) - p.rec_n0;
-                if (m >= 0 && m < p.rec_cap)
-                    p.rec[m * (int64_t)(p.rec_y < 0 ? p.ny : 1) * p.nx + (p.rec_y < 0 ? (int64_t)y * p.nx : 0) + x] =
-                        nxt;
-            }
+        if (REC && p.energy_on) {
+            const float d = nxt - c;
+            e = __fdividef(d * d, kap) - nxt * acc;
         }
     }
     if (REC && p.energy_on) {
@@ -113,7 +91,7 @@ cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)
 {
     if (p.ny > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
     dim3 grid((p.nx + 127) / 128, p.ny, p.nz);
-    const bool rec = sweep_extended(p);
+    const bool rec = p.energy_on != 0;
     if (R == 4 && rec)
         sweep_naive_kernel<4, true><<<grid, 128, 0, s>>>(p);
     else if (R == 4)

@@ -196,36 +196,73 @@ SweepParams Plan::params(int parity, int step_off) const
     s.amax = d_amax;
     s.growth = growth;
     s.src_bound = src_bound;
-    s.rec = rec;
     s.energy = rec_energy;
     s.energy_part = rec_part;
     s.energy_count = rec_count;
     s.rec_n0 = rec_n0;
     s.rec_cap = rec_cap;
-    s.rec_z = rec_mem ? rec_z : -1;
-    s.rec_y = rec_y;
     s.energy_on = rec_mem ? rec_energy_on : 0;
-    s.inj = inj;
-    s.inj_n0 = inj_n0;
-    s.inj_steps = inj_steps;
-    s.inj_reverse = inj_reverse;
-    s.inj_z = inj ? inj_z : -1;
-    s.inj_y = inj_y;
-    s.inj_scale = inj_scale;
-    s.absorb_w = absorb_w;
-    s.absorb_eta = absorb_eta;
+    // with an absorbing layer the source is added after the layer's pass
+    if (absorb_w > 0) s.src.on = 0;
     return s;
 }
 
+StepOps Plan::step_ops(int step_off) const
+{
+    StepOps o{};
+    o.nx = nx;
+    o.ny = ny;
+    o.nz = nz;
+    o.pitch = pitch;
+    o.plane = pitch * ny;
+    o.step_base = d_step;
+    o.step_off = step_off;
+    o.absorb_w = absorb_w;
+    o.absorb_eta = absorb_eta;
+    o.shell_points = absorb_shell;
+    o.save = absorb_save;
+    o.src = src;
+    o.inj = inj;
+    o.inj_n0 = inj_n0;
+    o.inj_steps = inj_steps;
+    o.inj_reverse = inj_reverse;
+    o.inj_z = inj ? inj_z : -1;
+    o.inj_y = inj_y;
+    o.inj_scale = inj_scale;
+    o.rec = rec;
+    o.scale = storage == STENCIL_FP32 ? nullptr : d_scale;
+    o.rec_n0 = rec_n0;
+    o.rec_cap = rec_cap;
+    o.rec_z = rec ? rec_z : -1;
+    o.rec_y = rec_y;
+    return o;
+}
+
+bool Plan::has_step_ops() const { return absorb_w > 0 || inj != nullptr || rec != nullptr; }
+
+// One time step: [layer save] sweep [layer apply, source, injection, record]
 cudaError_t Plan::launch_one(int parity, int step_off, cudaStream_t s) const
 {
     const SweepParams prm = params(parity, step_off);
-    if (tile.kernel == STENCIL_KERNEL_NAIVE) return launch_naive(R, prm, s);
-    TiledMaps m;
-    m.u_halo = maps_halo[parity];
-    m.up_core = maps_core[parity ^ 1];
-    m.k_core = map_kcore;
-    return launch_tiled(R, storage, tile.tx, tile.ty, m, prm, s);
+    const bool ops = has_step_ops();
+    StepOps o{};
+    cudaError_t e = cudaSuccess;
+    if (ops) {
+        o = step_ops(step_off);
+        e = launch_step_pre(o, buf[parity ^ 1], s);
+        if (e != cudaSuccess) return e;
+    }
+    if (tile.kernel == STENCIL_KERNEL_NAIVE) {
+        e = launch_naive(R, prm, s);
+    } else {
+        TiledMaps m;
+        m.u_halo = maps_halo[parity];
+        m.up_core = maps_core[parity ^ 1];
+        m.k_core = map_kcore;
+        e = launch_tiled(R, storage, tile.tx, tile.ty, m, prm, s);
+    }
+    if (e == cudaSuccess && ops) e = launch_step_post(o, buf[parity ^ 1], storage, s);
+    return e;
 }
 
 int Plan::enqueue_eager(int nsteps)
@@ -323,6 +360,8 @@ void Plan::release()
     drop_graphs();
     if (rec_mem) dev_free(rec_mem);
     rec_mem = nullptr;
+    if (absorb_save) dev_free(absorb_save);
+    absorb_save = nullptr;
     if (!user_owned) {
         for (auto &b : buf)
             if (b) dev_free(b);
@@ -576,6 +615,10 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     p->tune_mode = d->tune_mode;
     p->absorb_w = d->absorb_eta > 0.0 ? d->absorb_width : 0;
     p->absorb_eta = (float)d->absorb_eta;
+    if (p->absorb_w > 0 && d->storage != STENCIL_FP32) {
+        delete p;
+        return fail(STENCIL_EUNSUPPORTED, "the absorbing layer needs FP32 storage");
+    }
     auto bail = [&](int code) {
         p->release();
         delete p;
@@ -621,6 +664,13 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
         p->d_amax = reinterpret_cast<unsigned *>(sc + red_bytes + 4 * 4 * (size_t)d->nz);
     }
     p->device_bytes = (p->user_owned ? 0 : 2 * (int64_t)fbytes + (int64_t)kbytes) + (int64_t)scratch;
+    if (p->absorb_w > 0) {
+        // u^{n-1} of the layer's points, saved before each sweep
+        p->absorb_shell = shell_points(d->nx, d->ny, d->nz, p->absorb_w);
+        e = p->dev_alloc(reinterpret_cast<void **>(&p->absorb_save), sizeof(float) * (size_t)p->absorb_shell);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(absorbing layer)"));
+        p->device_bytes += (int64_t)sizeof(float) * p->absorb_shell;
+    }
 
     cudaStream_t s = p->stream;
     if ((e = cudaMemsetAsync(p->d_scratch, 0, scratch, s)) != cudaSuccess ||

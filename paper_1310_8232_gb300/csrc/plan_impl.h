@@ -70,6 +70,8 @@ struct Plan {
     // absorbing layer and plane injection
     int absorb_w = 0;
     float absorb_eta = 0.0f;
+    int64_t absorb_shell = 0;
+    float *absorb_save = nullptr;
     const float *inj = nullptr;
     int64_t inj_n0 = 0;
     int inj_steps = 0, inj_reverse = 0, inj_z = -1, inj_y = -1;
@@ -90,6 +92,8 @@ struct Plan {
     int load_velocity(const float *v, int on_device);
     SweepParams params(int parity, int step_off) const;
     cudaError_t launch_one(int parity, int step_off, cudaStream_t s) const;
+    StepOps step_ops(int step_off) const;
+    bool has_step_ops() const;
     int enqueue_eager(int nsteps);
     int enqueue(int nsteps);
     int capture_graphs();

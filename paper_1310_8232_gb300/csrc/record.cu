@@ -3,12 +3,13 @@
 // loop body beside the 3D model), both written by the sweep itself.
 //
 // Traces: the values u^{n+1} of a receiver plane z = rec_z (or one row y of
-// it) after each step, as the sweep computes them (FP32, before any 16-bit
-// storage rounding), [record][ny or 1][nx].
+// it) after each step, as stored (16-bit storage: times the plane's scale),
+// [record][ny or 1][nx], copied by a small kernel after the step.
 // Energy: E^{n+1/2} = sum_p (u^{n+1} - u^n)^2 / kappa - u^{n+1} Lambda(u^n)
 // (the quantity the scheme conserves without a source; dx^2 / dt^2 times the
-// physical discrete energy), summed per warp in FP32 per plane, per block in
-// FP64, and over blocks in block order by the last block of the launch.
+// physical discrete energy), summed inside the sweep: per warp in FP32 over
+// a ring of planes, per block in FP64, and over blocks in block order by the
+// last block of the launch.
 #include <algorithm>
 
 #include "plan_impl.h"
@@ -54,6 +55,8 @@ int stencil_record_start(stencil_plan_t h, const stencil_record_cfg *c)
     if (c->receiver_z < -1 || c->receiver_z >= p->nz) return fail(STENCIL_EINVAL, "receiver_z outside the grid");
     if (c->receiver_y < -1 || c->receiver_y >= p->ny) return fail(STENCIL_EINVAL, "receiver_y outside the grid");
     if (c->receiver_z < 0 && !c->energy) return fail(STENCIL_EINVAL, "nothing to record");
+    if (c->energy && (p->absorb_w > 0 || p->inj))
+        return fail(STENCIL_EUNSUPPORTED, "the energy is recorded for plans without an absorbing layer or injection");
     int rc = stencil_record_stop(h);
     if (rc) return rc;
     const int64_t per = c->receiver_z < 0 ? 0 : (int64_t)(c->receiver_y < 0 ? p->ny : 1) * p->nx;

@@ -1,8 +1,8 @@
 // Plane injection and the imaging condition: the pieces reverse-time
 // migration adds around the 3D-model sweep (the backward propagation of the
 // recorded traces and the zero-lag cross-correlation with the source
-// wavefield).  The injection itself runs inside the sweep (extended kernel
-// variants); these entry points set it up and run the imaging kernel.
+// wavefield).  The injection runs as a small kernel after each step
+// (plane_ops.cu); these entry points set it up and run the imaging kernel.
 #include "plan_impl.h"
 
 using namespace stencil;
@@ -32,6 +32,8 @@ int stencil_inject_start(stencil_plan_t h, const stencil_inject_cfg *c)
     if (c->z < 0 || c->z >= p->nz) return fail(STENCIL_EINVAL, "injection plane outside the grid");
     if (c->y < -1 || c->y >= p->ny) return fail(STENCIL_EINVAL, "injection row outside the grid");
     if (c->steps < 1) return fail(STENCIL_EINVAL, "steps must be >= 1");
+    if (p->rec_mem && p->rec_energy_on)
+        return fail(STENCIL_EUNSUPPORTED, "the energy is recorded for plans without injection");
     if (!std::isfinite(c->scale)) return fail(STENCIL_EINVAL, "scale must be finite");
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, c->data) != cudaSuccess || a.type != cudaMemoryTypeDevice) {

@@ -414,21 +414,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     const float2 oB =
                         __ffma2_rn(hi2(kap[h]), fB, __ffma2_rn(neg1, hi2(prev[h]), __fmul2_rn(two, hi2(cc))));
                     float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
-                    if (REC && p.absorb_w > 0) {
-                        // absorbing layer: (2u - (1 - eta) u^{n-1} + kappa Lambda) / (1 + eta),
-                        // formed as (plain update + eta u^{n-1}) / (1 + eta)
-                        const int gy = gy0 + h;
-                        const int dyz = min(min(gy, p.ny - 1 - gy), min(o, p.nz - 1 - o));
-                        if (min(dyz, min(gx, p.nx - 4 - gx)) < p.absorb_w) {
-                            float *nv = &nxt.x;
-                            const float *pv = &prev[h].x;
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                const float e = absorb_eta(p, min(dyz, min(gx + k, p.nx - 1 - gx - k)));
-                                nv[k] = fmaf(e, pv[k], nv[k]) * (1.0f / (1.0f + e));
-                            }
-                        }
-                    }
                     if (src_here && src_row == h && o == p.src.z) {
                         const double t = (double)n_level * p.src.dt;
                         const float add = (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
@@ -439,18 +424,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         else nxt.w += add;
                     }
                     const bool ok = x_ok && gy0 + h < p.ny;
-                    if (REC && o == p.inj_z && ok && (p.inj_y < 0 || p.inj_y == gy0 + h)) {
-                        const int64_t m = n_level - p.inj_n0;
-                        const int64_t idx = p.inj_reverse ? p.inj_steps - 1 - m : m;
-                        if (m >= 0 && idx >= 0 && idx < p.inj_steps) {
-                            const float *d = p.inj + idx * (int64_t)(p.inj_y < 0 ? p.ny : 1) * p.nx +
-                                             (p.inj_y < 0 ? (int64_t)(gy0 + h) * p.nx : 0) + gx;
-                            if (gx + 0 < p.nx) nxt.x += p.inj_scale * d[0];
-                            if (gx + 1 < p.nx) nxt.y += p.inj_scale * d[1];
-                            if (gx + 2 < p.nx) nxt.z += p.inj_scale * d[2];
-                            if (gx + 3 < p.nx) nxt.w += p.inj_scale * d[3];
-                        }
-                    }
                     if (REC && p.energy_on && ok) {
                         // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa - u^{n+1} Lambda(u^n)
                         const float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
@@ -467,17 +440,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             eB.y = 0.f;
                         }
                         esum = __fadd2_rn(esum, __fadd2_rn(eA, eB));
-                    }
-                    if (REC && o == p.rec_z && ok && (p.rec_y < 0 || p.rec_y == gy0 + h)) {
-                        const int64_t m = n_level - p.rec_n0;
-                        if (m >= 0 && m < p.rec_cap) {
-                            float *t = p.rec + m * (int64_t)(p.rec_y < 0 ? p.ny : 1) * p.nx +
-                                       (p.rec_y < 0 ? (int64_t)(gy0 + h) * p.nx : 0) + gx;
-                            const float u1[4] = {nxt.x, nxt.y, nxt.z, nxt.w};
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                if (gx + k < p.nx) t[k] = u1[k];
-                        }
                     }
                     if constexpr (!S::F32) {
                         if (ok)
@@ -545,7 +507,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
 }
 
 // One shot per launch: block (tile, z-chunk) from the grid position.  REC:
-// the variant that also writes receiver traces and the step's energy.
+// the variant that also sums the step's energy.
 template <int R, int TX, int TY, typename E, bool REC = false>
 __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
     sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,

@@ -78,7 +78,7 @@ struct Inst {
             q.tiles_x = tiles_x;
             q.zchunk = zc;
             dim3 grid(tiles_x * tiles_y, nzc);
-            if (sweep_extended(q))
+            if (q.energy_on)
                 sweep_tiled_kernel<R, TX, TY, E, true><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
             else
                 sweep_tiled_kernel<R, TX, TY, E, false><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);

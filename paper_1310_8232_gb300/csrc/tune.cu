@@ -211,10 +211,7 @@ static cudaError_t sweep_view(const Plan *p, const View &v, int parity, cudaStre
     prm.kappa = p->kappa + off;
     prm.zchunk = std::min(v.c.zc, v.nzs);
     prm.src.on = 0;
-    prm.rec_z = -1;                 // selection sweeps time the plain sweep
-    prm.energy_on = 0;
-    prm.inj_z = -1;
-    prm.absorb_w = 0;
+    prm.energy_on = 0;              // selection sweeps time the plain sweep
     return launch_tiled(p->R, p->storage, v.c.tx, v.c.ty, v.maps[parity], prm, s);
 }
 

@@ -92,9 +92,9 @@ def test_injection_matches_oracle_forward_and_reversed(env, k):
         check(out, ref)
 
 
-def test_extended_sweep_with_nothing_on_is_the_plain_sweep(env):
-    """Recording switches in the extended kernel; with no layer and no
-    injection its fields are bit for bit the plain kernel's."""
+def test_recording_leaves_the_fields_bit_for_bit(env):
+    """The record pass after each step only reads: the fields are bit for
+    bit those of a plan that records nothing."""
     torch, st = env
     nx, ny, nz = SHAPE
     v = workloads.layered_velocity(nx, ny, nz, seed=34)
@@ -147,3 +147,25 @@ def test_one_shot_migration_matches_oracle(env, k):
     ref_img, ref_tr, _ = oracle_rtm.migrate(v, DX, dt, R, T, src, zr, snap, absorb=absorb, f=25.0)
     check(traces.cpu().numpy(), ref_tr, 2e-5)
     check(image.cpu().numpy(), ref_img, 1e-4)
+
+
+def test_unsupported_combinations_are_refused(env):
+    torch, st = env
+    nx, ny, nz = 24, 20, 18
+    v = workloads.constant_velocity(nx, ny, nz, 2000.0)
+    dt = workloads.time_step(oracle.cfl_limit(4), DX, 2000.0)
+    s = stream(torch)
+    with pytest.raises(st.StencilError) as ei:            # the layer needs FP32 storage
+        st.stencil_plan(st.make_desc(v, dt, radius=4, storage=1, absorb=(4, 0.2), stream=s))
+    assert ei.value.code == st.STENCIL_EUNSUPPORTED
+    plan = st.stencil_plan(st.make_desc(v, dt, radius=4, absorb=(4, 0.2), stream=s))
+    try:                                                   # energy only without layer / injection
+        with pytest.raises(st.StencilError) as ei:
+            st.stencil_record_start(plan, energy=True, capacity=4)
+        assert ei.value.code == st.STENCIL_EUNSUPPORTED
+    finally:
+        st.stencil_destroy(plan)
+    d = st.make_desc(v, dt, radius=4, absorb=(4, 0.2), stream=s)
+    with pytest.raises(st.StencilError) as ei:             # batches run the plain sweep
+        st.stencil_batch_create([d])
+    assert ei.value.code == st.STENCIL_EUNSUPPORTED
