@@ -101,18 +101,8 @@ struct Inst {
     }
 };
 
-// Calls F<R, TX, TY>::fn(...) for the runtime (R, tx, ty); the tile list is
-// the one the library is built with for this storage type.
-#define STENCIL_TILE_SWITCH(E, TILES, CALL, MISS)                                   \
-    do {                                                                            \
-        if (R == 4) {                                                               \
-            TILES(4, E, CALL)                                                       \
-        } else if (R == 5) {                                                        \
-            TILES(5, E, CALL)                                                       \
-        }                                                                           \
-        MISS;                                                                       \
-    } while (0)
-
+// One tile of a unit's tile list: CALL with I = the tile's instantiation
+// when the runtime (tx, ty) matches.
 #define STENCIL_ONE(R_, E, TX_, TY_, CALL) \
     if (tx == TX_ && ty == TY_) { using I = Inst<R_, TX_, TY_, E>; CALL; }
 
