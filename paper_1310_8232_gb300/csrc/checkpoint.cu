@@ -134,7 +134,7 @@ int stencil_checkpoint(stencil_plan_t h, void *dst, uint64_t bytes, int32_t on_d
     int n = 0;
     pieces(p, pc, &n);
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = cudaMemcpy2DAsync(at, pc[i].row_bytes, pc[i].dev, pc[i].dev_pitch, pc[i].row_bytes, pc[i].rows, out,
+        e = memcpy_rows(at, pc[i].row_bytes, pc[i].dev, pc[i].dev_pitch, pc[i].row_bytes, pc[i].rows, out,
                               p->stream);
         at += pc[i].row_bytes * pc[i].rows;
     }
@@ -181,7 +181,7 @@ int stencil_restore(stencil_plan_t h, const void *src, uint64_t bytes, int32_t o
     const char *at = static_cast<const char *>(src) + sizeof hd;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     for (int i = 0; i < n && e == cudaSuccess; ++i) {
-        e = cudaMemcpy2DAsync(pc[i].dev, pc[i].dev_pitch, at, pc[i].row_bytes, pc[i].row_bytes, pc[i].rows, kind,
+        e = memcpy_rows(pc[i].dev, pc[i].dev_pitch, at, pc[i].row_bytes, pc[i].row_bytes, pc[i].rows, kind,
                               p->stream);
         at += pc[i].row_bytes * pc[i].rows;
     }

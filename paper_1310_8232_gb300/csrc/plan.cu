@@ -385,7 +385,7 @@ void Plan::release()
 int Plan::load_velocity(const float *v, int on_device)
 {
     cudaStream_t s = stream;
-    cudaError_t e = cudaMemcpy2DAsync(kappa, pitch * sizeof(float), v, (size_t)nx * sizeof(float),
+    cudaError_t e = memcpy_rows(kappa, pitch * sizeof(float), v, (size_t)nx * sizeof(float),
                                       (size_t)nx * sizeof(float), (size_t)ny * nz,
                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail_cuda(e, "velocity copy");
@@ -776,7 +776,7 @@ static int copy_out(Plan *p, int which, float *out, int on_device)
     const float *src = nullptr;
     int rc = p->fp32_level(which, &src);
     if (rc) return rc;
-    cudaError_t e = cudaMemcpy2DAsync(out, (size_t)p->nx * sizeof(float), src, p->pitch * sizeof(float),
+    cudaError_t e = memcpy_rows(out, (size_t)p->nx * sizeof(float), src, p->pitch * sizeof(float),
                                       (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "field copy out");
@@ -840,7 +840,7 @@ int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, in
                 e = cudaMemsetAsync(p->d_scale + (int64_t)slot * p->nz, 0, sizeof(float) * p->nz, p->stream);
         } else {
             float *stage = p->storage == STENCIL_FP32 ? static_cast<float *>(dst) : p->staging[0];
-            e = cudaMemcpy2DAsync(stage, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
+            e = memcpy_rows(stage, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
                                   (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream);
             if (e == cudaSuccess && p->storage != STENCIL_FP32)

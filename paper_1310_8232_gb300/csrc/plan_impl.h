@@ -21,6 +21,15 @@ int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz);
 int check_tile(int R, int storage, const stencil_tile &t);
 extern thread_local std::string g_last_error;
 
+// Row-by-row copy between pitched layouts; one flat copy when both sides
+// are dense (a 2D copy of many short rows is much slower than a flat one).
+inline cudaError_t memcpy_rows(void *dst, size_t dpitch, const void *src, size_t spitch, size_t row_bytes,
+                               size_t rows, cudaMemcpyKind kind, cudaStream_t s)
+{
+    if (dpitch == row_bytes && spitch == row_bytes) return cudaMemcpyAsync(dst, src, row_bytes * rows, kind, s);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row_bytes, rows, kind, s);
+}
+
 struct Plan {
     int dev = 0;
     cudaMemPool_t pool = nullptr;         // set: stream-ordered allocations from this pool

@@ -134,7 +134,7 @@ int Server::read_back(Plan *p, float *out)
     int k = 0;
     for (int64_t r0 = 0; r0 < rows; r0 += per, ++k) {
         const int64_t n = std::min(per, rows - r0);
-        cudaError_t e = cudaMemcpy2DAsync(bounce[k & 1], row_bytes, src + r0 * p->pitch, p->pitch * sizeof(float),
+        cudaError_t e = memcpy_rows(bounce[k & 1], row_bytes, src + r0 * p->pitch, p->pitch * sizeof(float),
                                           row_bytes, (size_t)n, cudaMemcpyDeviceToHost, retire_stream);
         if (e == cudaSuccess) e = cudaEventRecord(bounce_ev[k & 1], retire_stream);
         if (e != cudaSuccess) return fail_cuda(e, "read-back");
