@@ -6,7 +6,9 @@
 // fit under the memory budget, keeps every admitted shot's wavefields
 // resident, and advances all resident shots together, chunk_steps time steps
 // per iteration, with the grouped kernel (one launch per step over all
-// shots' tiles).  Shots that reach their step count retire: the final field
+// shots' tiles).  Each iteration launches the resident shots' steps first
+// and creates the newly admitted shots' plans on a second stream while the
+// GPU runs them; the new shots join at the next iteration.  Shots that reach their step count retire: the final field
 // is copied to the caller's buffer and the shot's memory is freed by a
 // second thread on its own stream (so the engine keeps stepping the other
 // shots meanwhile), and the slot goes to the next request.  Device memory
@@ -63,6 +65,7 @@ struct Server {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t retire_stream = nullptr;
+    cudaStream_t admit_stream = nullptr;      // plan creation, overlapping the engine's steps
     cudaMemPool_t pool = nullptr;
     int64_t budget = 0;
     Clock::time_point t0;
@@ -188,11 +191,46 @@ void Server::run()
     cudaSetDevice(dev);
     bool rebuild = false;
     for (;;) {
-        // ---- admission -------------------------------------------------
+        // ---- this iteration's steps for the resident shots, launched first so
+        //      that admission below overlaps them ---------------------------
+        const bool stepping = !resident.empty();
+        auto it0 = Clock::now();
+        int rc = STENCIL_OK;
+        if (stepping) {
+            if (rebuild) {
+                std::vector<Plan *> plans;
+                std::vector<int64_t> n_end;
+                for (Request *r : resident) {
+                    plans.push_back(r->plan);
+                    n_end.push_back(r->nsteps);
+                }
+                group.zchunk = group_zchunk(group.R, group.storage, group.tx, group.ty, plans);
+                TiledInfo info{};
+                tiled_config(group.R, group.storage, group.tx, group.ty, &info);
+                if (info.zmax) group.zchunk = std::min(group.zchunk, info.zmax);
+                rc = group.build(plans, n_end);
+                if (rc) {
+                    engine_error = rc;
+                    for (Request *r : resident) retire(r, rc);
+                    resident.clear();
+                    continue;
+                }
+                rebuild = false;
+                const auto b1 = Clock::now();
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    stats.build_s += std::chrono::duration<double>(b1 - it0).count();
+                }
+                it0 = b1;
+            }
+            rc = group.step(cfg.chunk_steps);
+        }
+
+        // ---- admission (plans made on the admission stream) ----------------
         std::vector<Request *> admit;
         {
             std::unique_lock<std::mutex> lock(mu);
-            if (resident.empty())
+            if (!stepping)
                 cv.wait_for(lock, std::chrono::milliseconds(20), [&] { return stopping || !queue.empty(); });
             if (stopping) {
                 for (Request *r : queue) {
@@ -203,7 +241,7 @@ void Server::run()
                     stats.failed += 1;
                 }
                 queue.clear();
-                if (resident.empty()) {
+                if (!stepping) {
                     cv.notify_all();
                     return;
                 }
@@ -219,94 +257,70 @@ void Server::run()
                 admit.push_back(r);
             }
         }
+        std::vector<Request *> admitted;
         for (Request *r : admit) {
             const auto a0 = Clock::now();
             stencil_desc d = r->desc;
-            d.cuda_stream = stream;
+            d.cuda_stream = admit_stream;
             d.tune_mode = STENCIL_TUNE_NONE;
             d.graph_steps = 0;
             d.storage = cfg.storage;
             d.radius = cfg.radius;
             d.tile = group.tx ? stencil_tile{STENCIL_KERNEL_TILED, group.tx, group.ty, -1} : d.tile;
             Plan *p = nullptr;
-            int rc = plan_create(&d, &p, pool);
+            const int arc = plan_create(&d, &p, pool);   // synchronous on the admission stream
             {
                 std::lock_guard<std::mutex> lock(mu);
                 r->t_admit = now();
                 stats.admitted += 1;
                 stats.admit_s += std::chrono::duration<double>(Clock::now() - a0).count();
             }
-            if (rc) {
-                retire(r, rc);
+            if (arc) {
+                retire(r, arc);
                 continue;
             }
+            p->stream = stream;                 // the group's stream from here on
             r->plan = p;
             r->velocity.clear();
             r->velocity.shrink_to_fit();
-            resident.push_back(r);
-            rebuild = true;
+            admitted.push_back(r);
         }
-        if (resident.empty()) continue;
 
-        // ---- one engine iteration over every resident shot ---------------
-        auto it0 = Clock::now();
-        if (rebuild) {
-            std::vector<Plan *> plans;
-            std::vector<int64_t> n_end;
-            for (Request *r : resident) {
-                plans.push_back(r->plan);
-                n_end.push_back(r->nsteps);
-            }
-            group.zchunk = group_zchunk(group.R, group.storage, group.tx, group.ty, plans);
-            TiledInfo info{};
-            tiled_config(group.R, group.storage, group.tx, group.ty, &info);
-            if (info.zmax) group.zchunk = std::min(group.zchunk, info.zmax);
-            int rc = group.build(plans, n_end);
-            if (rc) {
-                engine_error = rc;
-                for (Request *r : resident) retire(r, rc);
-                resident.clear();
-                continue;
-            }
-            rebuild = false;
-            const auto b1 = Clock::now();
+        // ---- end of the iteration: shots that reached their count retire ----
+        if (stepping) {
+            cudaError_t e = cudaStreamSynchronize(stream);
+            if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "engine iteration");
             {
                 std::lock_guard<std::mutex> lock(mu);
-                stats.build_s += std::chrono::duration<double>(b1 - it0).count();
+                stats.iterations += 1;
+                stats.busy_s += std::chrono::duration<double>(Clock::now() - it0).count();
             }
-            it0 = b1;
-        }
-        int rc = group.step(cfg.chunk_steps);
-        cudaError_t e = cudaStreamSynchronize(stream);
-        if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "engine iteration");
-        {
-            std::lock_guard<std::mutex> lock(mu);
-            stats.iterations += 1;
-            stats.busy_s += std::chrono::duration<double>(Clock::now() - it0).count();
-        }
-        std::vector<Request *> keep;
-        for (size_t i = 0; i < resident.size(); ++i) {
-            Request *r = resident[i];
-            Plan *p = r->plan;
-            const int pb = group.h_shots[i].parity_base;
-            p->steps_done = std::min<int64_t>(p->steps_done + cfg.chunk_steps, r->nsteps);
-            p->cur = (int)((p->steps_done + pb) & 1);
-            {
-                std::lock_guard<std::mutex> lock(mu);
-                r->steps_done = p->steps_done;
+            std::vector<Request *> keep;
+            for (size_t i = 0; i < resident.size(); ++i) {
+                Request *r = resident[i];
+                Plan *p = r->plan;
+                const int pb = group.h_shots[i].parity_base;
+                p->steps_done = std::min<int64_t>(p->steps_done + cfg.chunk_steps, r->nsteps);
+                p->cur = (int)((p->steps_done + pb) & 1);
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    r->steps_done = p->steps_done;
+                }
+                if (rc != STENCIL_OK) {
+                    retire(r, rc);
+                    rebuild = true;
+                } else if (p->steps_done >= r->nsteps) {
+                    int drc = p->check_device_error();
+                    retire(r, drc);
+                    rebuild = true;
+                } else {
+                    keep.push_back(r);
+                }
             }
-            if (rc != STENCIL_OK) {
-                retire(r, rc);
-                rebuild = true;
-            } else if (p->steps_done >= r->nsteps) {
-                int drc = p->check_device_error();
-                retire(r, drc);
-                rebuild = true;
-            } else {
-                keep.push_back(r);
-            }
+            resident.swap(keep);
         }
-        resident.swap(keep);
+        for (Request *r : admitted) resident.push_back(r);
+        if (!admitted.empty()) rebuild = true;
     }
 }
 
@@ -372,12 +386,18 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
         if (s->own_stream) cudaStreamDestroy(s->stream);
         return fail_cuda(e, "cudaStreamCreate(retire)");
     }
+    if ((e = cudaStreamCreateWithFlags(&s->admit_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaStreamDestroy(s->retire_stream);
+        if (s->own_stream) cudaStreamDestroy(s->stream);
+        return fail_cuda(e, "cudaStreamCreate(admission)");
+    }
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.handleTypes = cudaMemHandleTypeNone;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = s->dev;
     if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) {
+        cudaStreamDestroy(s->admit_stream);
         cudaStreamDestroy(s->retire_stream);
         if (s->own_stream) cudaStreamDestroy(s->stream);
         return fail_cuda(e, "cudaMemPoolCreate");
@@ -390,6 +410,7 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
                 if (s->bounce_ev[j]) cudaEventDestroy(s->bounce_ev[j]);
             }
             cudaMemPoolDestroy(s->pool);
+            cudaStreamDestroy(s->admit_stream);
             cudaStreamDestroy(s->retire_stream);
             if (s->own_stream) cudaStreamDestroy(s->stream);
             return fail_cuda(e, "pinned read-back buffers");
@@ -514,6 +535,8 @@ int shot_server_destroy(shot_server_t h)
     s->group.release();
     cudaStreamSynchronize(s->retire_stream);
     cudaStreamDestroy(s->retire_stream);
+    cudaStreamSynchronize(s->admit_stream);
+    cudaStreamDestroy(s->admit_stream);
     for (int k = 0; k < 2; ++k) {
         if (s->bounce[k]) cudaFreeHost(s->bounce[k]);
         if (s->bounce_ev[k]) cudaEventDestroy(s->bounce_ev[k]);
