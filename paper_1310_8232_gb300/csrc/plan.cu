@@ -877,11 +877,15 @@ int stencil_set_velocity(stencil_plan_t h, const float *velocity, int32_t on_dev
         else v_src = *vs;
         if (e != cudaSuccess) return fail_cuda(e, "source velocity read");
     }
+    const double old_scale = p->src.scale;
+    const float old_bound = p->src_bound, old_growth = p->growth;
     int rc = p->load_velocity(velocity, on_device);
     if (rc) return rc;
     p->src.scale = p->src_amp * (double)v_src * (double)v_src * p->dt * p->dt;
     p->src_bound = (float)(std::fabs(p->src.scale) * (1.0 + 1e-6));
-    p->drop_graphs();   // captured launches carry the old source scale and growth bound
+    // captured launches carry the source scale and the growth bound by value:
+    // recapture only when a new model changes them (kappa is read in place)
+    if (p->src.scale != old_scale || p->src_bound != old_bound || p->growth != old_growth) p->drop_graphs();
     return STENCIL_OK;
 }
 

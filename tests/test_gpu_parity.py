@@ -373,3 +373,34 @@ def test_automatic_kernel_choice_by_grid_size(env):
             assert st.stencil_get_stats(plan).tile.kernel == kernel, (shape, storage)
         finally:
             st.stencil_destroy(plan)
+
+
+def test_set_velocity_replaces_the_model_with_graphs_captured(env):
+    """A new model through stencil_set_velocity gives what a fresh plan on
+    that model gives, whether or not its source-point velocity changed (the
+    captured graphs are kept only when nothing they carry changed)."""
+    torch, st = env
+    nx, ny, nz, R = 48, 40, 36, 5
+    src = (20, 20, 18)
+    a = workloads.layered_velocity(nx, ny, nz, seed=51)
+    b = a.copy()
+    b[:, :, : nx // 2] *= 0.9                      # same velocity at the source, different elsewhere
+    c = workloads.layered_velocity(nx, ny, nz, seed=52)   # different at the source too
+    dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(max(a.max(), c.max())))
+
+    def fresh(v):
+        got, _, _ = run_gpu(env, v, dt, R, 24, src=src, graph_steps=6, on_device=False)
+        return got
+
+    d = st.make_desc(a, dt, radius=R, src=src, tile=DEFAULT_TILED, graph_steps=6, stream=cur_stream(torch))
+    plan = st.stencil_plan(d)
+    try:
+        st.stencil_step(plan, 12)                   # graphs captured on model a
+        for v in (b, c, a):
+            st.stencil_set_velocity(plan, v)
+            st.stencil_set_fields(plan, None, None, 0)
+            out = np.empty_like(v)
+            st.stencil_run(plan, 24, out)
+            assert np.array_equal(out, fresh(v))
+    finally:
+        st.stencil_destroy(plan)
