@@ -95,3 +95,17 @@ def test_original_block_global_min():
 def test_quality_rejects_nonpositive_min():
     with pytest.raises(ValueError):
         selection.quality(0.0, 1.0)
+
+
+def test_paper_table1_and_table3_percentages():
+    """Tables 1 and 3: every printed percentage is the quality-style relative
+    excess value / reference - 1 (the arithmetic the selection report uses),
+    rounded or truncated to the printed decimals."""
+    rows = read_golden("paper_table1_table3_ratios.txt")
+    assert len(rows) == 11
+    for table, what, value, ref, printed, decimals in rows:
+        pct = 100.0 * selection.quality(float(ref), float(value))
+        step = 10.0 ** -int(decimals)
+        assert abs(pct - float(printed)) < step, (table, what, pct, printed)
+        # the inverse ratio would be far off: the formula's direction is pinned
+        assert abs(100.0 * selection.quality(float(value), float(ref)) - float(printed)) > 1.0
