@@ -296,6 +296,19 @@ STENCIL_API int stencil_inject_stop(stencil_plan_t p);
  * plan's stream (returns at once).  16 B per point of HBM traffic. */
 STENCIL_API int stencil_image_accumulate(stencil_plan_t p, const float *snapshot, float *image, float scale);
 
+/* ---- failure-path testing ---------------------------------------------
+ * Every shared-memory wait of the tiled sweep is bounded; a wait that runs
+ * out sets the plan's error word, its thread block leaves after the copies
+ * it issued have landed (also bounded), and the next synchronising call
+ * returns STENCIL_ETIMEOUT and clears the word, so the plan stays usable.
+ * This hook exercises that path without any GPU fault: with enable = 1 the
+ * first copy of every block is expected to bring 16 more bytes than it
+ * does, so that block's first wait runs out after wait_ns nanoseconds (0 =
+ * the default 2 s).  enable = 0 restores normal sweeps (wait_ns stays the
+ * wait limit).  Tiled kernel only (STENCIL_EUNSUPPORTED otherwise).  The
+ * paper has no counterpart; for tests of the error path. */
+STENCIL_API int stencil_debug_wait_fault(stencil_plan_t p, int32_t enable, uint32_t wait_ns);
+
 /* ---- checkpoint / restore ---------------------------------------------
  * The time loop's state (Sec. 2, Algorithm 1): the two levels u^n and
  * u^{n-1} in the plan's storage encoding, the step n (the source reads

@@ -149,6 +149,7 @@ _lib.stencil_record_stop.argtypes = [_P]
 _lib.stencil_inject_start.argtypes = [_P, ctypes.POINTER(stencil_inject_cfg)]
 _lib.stencil_inject_stop.argtypes = [_P]
 _lib.stencil_image_accumulate.argtypes = [_P, _P, _P, ctypes.c_float]
+_lib.stencil_debug_wait_fault.argtypes = [_P, _I, ctypes.c_uint32]
 _lib.stencil_checkpoint_size.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64)]
 _lib.stencil_checkpoint.argtypes = [_P, _P, ctypes.c_uint64, _I]
 _lib.stencil_restore.argtypes = [_P, _P, ctypes.c_uint64, _I]
@@ -321,6 +322,10 @@ def stencil_image_accumulate(plan: int, snapshot, image, scale: float = 1.0) -> 
     if not (da and db):
         raise ValueError("snapshot and image must be CUDA tensors")
     _check(_lib.stencil_image_accumulate(plan, a, b, float(scale)))
+
+
+def stencil_debug_wait_fault(plan: int, enable: bool, wait_ns: int = 0) -> None:
+    _check(_lib.stencil_debug_wait_fault(plan, int(bool(enable)), int(wait_ns)))
 
 
 def stencil_checkpoint_size(plan: int) -> int:
@@ -556,7 +561,7 @@ EXPORTED = [
     "stencil_sync", "stencil_get_field", "stencil_set_fields", "stencil_set_velocity",
     "stencil_get_stats", "stencil_checkpoint_size", "stencil_checkpoint", "stencil_restore",
     "stencil_record_cfg_init", "stencil_record_start", "stencil_record_read", "stencil_record_stop",
-    "stencil_inject_start", "stencil_inject_stop", "stencil_image_accumulate",
+    "stencil_inject_start", "stencil_inject_stop", "stencil_image_accumulate", "stencil_debug_wait_fault",
     "stencil_energy", "stencil_rel_l2", "stencil_cfl_limit", "stencil_last_error",
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
     "stencil_tile_info", "stencil_batch_create", "stencil_batch_run", "stencil_batch_sync",

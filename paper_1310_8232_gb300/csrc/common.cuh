@@ -88,6 +88,11 @@ struct SweepParams {
     int64_t rec_n0;
     int32_t rec_cap;
     int32_t energy_on;
+    // failure-path testing: limit of every shared-memory wait (0 = 2 s), and
+    // extra bytes the first u copy of each block is expected to bring (> 0
+    // makes that wait run out)
+    uint32_t wait_ns;
+    uint32_t fault_tx;
 };
 
 // A shot of a grouped launch: its tensor maps (by parity of the level),

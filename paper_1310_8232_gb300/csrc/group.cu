@@ -82,6 +82,7 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
         g.prm = p->params(0, 0);
         g.prm.zchunk = zchunk;
         g.prm.energy_on = 0;        // grouped launches run the plain sweep
+        g.prm.fault_tx = 0;
         g.buf[0] = p->buf[0];
         g.buf[1] = p->buf[1];
         g.n_end = n_end[i];

@@ -204,6 +204,8 @@ SweepParams Plan::params(int parity, int step_off) const
     s.energy_on = rec_mem ? rec_energy_on : 0;
     // with an absorbing layer the source is added after the layer's pass
     if (absorb_w > 0) s.src.on = 0;
+    s.wait_ns = wait_ns;
+    s.fault_tx = fault_tx;
     return s;
 }
 
@@ -960,6 +962,20 @@ int stencil_tile_info(int32_t radius, int32_t storage, int32_t tx, int32_t ty, i
     if (smem_bytes) *smem_bytes = info.smem;
     if (threads) *threads = info.threads;
     return 1;
+}
+
+int stencil_debug_wait_fault(stencil_plan_t h, int32_t enable, uint32_t wait_ns)
+{
+    if (!h) return fail(STENCIL_EINVAL, "null plan");
+    Plan *p = reinterpret_cast<Plan *>(h);
+    cudaSetDevice(p->dev);
+    if (p->tile.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EUNSUPPORTED, "the hook needs the tiled kernel");
+    int rc = p->check_device_error();
+    if (rc) return rc;
+    p->fault_tx = enable ? 16u : 0u;
+    p->wait_ns = wait_ns;
+    p->drop_graphs();               // captured launches carry the parameters by value
+    return STENCIL_OK;
 }
 
 const char *stencil_last_error(void) { return g_last_error.c_str(); }

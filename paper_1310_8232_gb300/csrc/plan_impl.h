@@ -81,6 +81,8 @@ struct Plan {
     float absorb_eta = 0.0f;
     int64_t absorb_shell = 0;
     float *absorb_save = nullptr;
+    // failure-path testing (stencil_debug_wait_fault)
+    uint32_t fault_tx = 0, wait_ns = 0;
     const float *inj = nullptr;
     int64_t inj_n0 = 0;
     int inj_steps = 0, inj_reverse = 0, inj_z = -1, inj_y = -1;

@@ -182,6 +182,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     uint64_t *full_a = full_u + S::SU;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + S::FLAG_OFF);
 
+    const uint64_t wait_limit = p.wait_ns ? p.wait_ns : 2000000000ull;
     const int tid = threadIdx.x;
     const int x0 = bx * TX;
     const int y0 = by * TY;
@@ -194,7 +195,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
 
     auto issue_u = [&](int t) {               // plane pz0 + t into stage t % SU
         const int st = t % S::SU;
-        mbar_arrive_expect_tx(&full_u[st], S::U_BYTES);
+        mbar_arrive_expect_tx(&full_u[st], S::U_BYTES + (t == 0 ? p.fault_tx : 0u));
         tma_load_3d(su + st * S::U_STAGE, map_u, &full_u[st], x0 - S::HX, y0 - R, pz0 + t);
     };
     auto issue_a = [&](int ja) {              // u^{n-1} and kappa of output z0 + ja into stage ja % SA
@@ -284,7 +285,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
             constexpr int K = decltype(kc)::value;          // slot of plane i
             const int i = i0 + K;
             if (i >= nin) return;                           // block-uniform
-            if (!mbar_wait(&full_u[su_stage], su_phase, p.err)) *abort_flag = 1;
+            if (!mbar_wait(&full_u[su_stage], su_phase, p.err, wait_limit)) *abort_flag = 1;
             const E *pl = reinterpret_cast<const E *>(su + su_stage * S::U_STAGE) + own;
             const float sgi = S::F32 ? 1.0f : sig_in[i];
             // column of the thread's x group: rows -R .. ROWS-1+R around row 0
@@ -386,7 +387,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 constexpr int KF = (K + 1) % S::RING;             // slot of plane i - R
                 const float2 cR = make_float2(wf<R>(R), wf<R>(R));
                 const int ja = i - 2 * R;
-                if (!mbar_wait(&full_a[sa_stage], sa_phase, p.err)) *abort_flag = 1;
+                if (!mbar_wait(&full_a[sa_stage], sa_phase, p.err, wait_limit)) *abort_flag = 1;
                 const float sgp = S::F32 ? 1.0f : sig_prev[ja];
                 float4 prev[S::ROWS], kap[S::ROWS];
 #pragma unroll

@@ -212,6 +212,7 @@ static cudaError_t sweep_view(const Plan *p, const View &v, int parity, cudaStre
     prm.zchunk = std::min(v.c.zc, v.nzs);
     prm.src.on = 0;
     prm.energy_on = 0;              // selection sweeps time the plain sweep
+    prm.fault_tx = 0;
     return launch_tiled(p->R, p->storage, v.c.tx, v.c.ty, v.maps[parity], prm, s);
 }
 
