@@ -280,7 +280,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     int done = 0;                           // planes fully processed (block-uniform)
 
     for (int i0 = 0; i0 < nin; i0 += S::RING) {
-        float2 esum = make_float2(0.f, 0.f);    // REC: energy terms of this group of RING planes
+        float2 ekin = make_float2(0.f, 0.f);    // REC: energy terms of this group of RING planes
+        float2 epot = make_float2(0.f, 0.f);
         auto body = [&](auto kc) {
             constexpr int K = decltype(kc)::value;          // slot of plane i
             const int i = i0 + K;
@@ -426,21 +427,23 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     }
                     const bool ok = x_ok && gy0 + h < p.ny;
                     if (REC && p.energy_on && ok) {
-                        // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa - u^{n+1} Lambda(u^n)
-                        const float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
-                        const float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
-                        const float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
-                        const float2 rA = make_float2(__fdividef(1.0f, kap[h].x), __fdividef(1.0f, kap[h].y));
-                        const float2 rB = make_float2(__fdividef(1.0f, kap[h].z), __fdividef(1.0f, kap[h].w));
-                        float2 eA = __ffma2_rn(__fmul2_rn(dA, dA), rA, __fmul2_rn(neg1, __fmul2_rn(uA, fA)));
-                        float2 eB = __ffma2_rn(__fmul2_rn(dB, dB), rB, __fmul2_rn(neg1, __fmul2_rn(uB, fB)));
-                        if (gx + 4 > p.nx) {              // ragged right edge: points beyond nx
+                        // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa (into ekin) and
+                        // u^{n+1} Lambda(u^n) (into epot); points beyond nx count zero
+                        float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
+                        float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
+                        float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
+                        if (gx + 4 > p.nx) {
                             const int nv = p.nx - gx;     // 1 .. 3
-                            if (nv < 2) eA.y = 0.f;
-                            if (nv < 3) eB.x = 0.f;
-                            eB.y = 0.f;
+                            if (nv < 2) uA.y = dA.y = 0.f;
+                            if (nv < 3) uB.x = dB.x = 0.f;
+                            uB.y = dB.y = 0.f;
                         }
-                        esum = __fadd2_rn(esum, __fadd2_rn(eA, eB));
+                        const float2 rA = make_float2(rcp_approx(kap[h].x), rcp_approx(kap[h].y));
+                        const float2 rB = make_float2(rcp_approx(kap[h].z), rcp_approx(kap[h].w));
+                        ekin = __ffma2_rn(__fmul2_rn(dA, dA), rA, ekin);
+                        ekin = __ffma2_rn(__fmul2_rn(dB, dB), rB, ekin);
+                        epot = __ffma2_rn(uA, fA, epot);
+                        epot = __ffma2_rn(uB, fB, epot);
                     }
                     if constexpr (!S::F32) {
                         if (ok)
@@ -486,7 +489,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
         Unroll<0, S::RING>::run(body);
         if (REC && p.energy_on) {
             // the warp's FP32 sum over these planes, added in FP64 by lane 0
-            float e = esum.x + esum.y;
+            float e = (ekin.x + ekin.y) - (epot.x + epot.y);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
             if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
