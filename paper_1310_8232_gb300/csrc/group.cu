@@ -133,6 +133,7 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
 
 int Group::step(int k)
 {
+    TraceRange tr("grouped steps");
     if (n_shots == 0 || k <= 0) return STENCIL_OK;
     cudaError_t e;
     auto enqueue = [&](int steps) -> cudaError_t {

@@ -590,6 +590,7 @@ int check_tile(int R, int storage, const stencil_tile &t)
 
 int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
 {
+    TraceRange tr("plan_create");
     int rc = validate_desc(d);
     if (rc) return rc;
     int dev = 0;
@@ -768,6 +769,7 @@ int stencil_destroy(stencil_plan_t h)
 int stencil_step(stencil_plan_t h, int32_t nsteps)
 {
     if (!h) return fail(STENCIL_EINVAL, "null plan");
+    TraceRange tr("stencil_step");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
     return p->enqueue(nsteps);
@@ -788,6 +790,7 @@ static int copy_out(Plan *p, int which, float *out, int on_device)
 int stencil_run(stencil_plan_t h, int32_t nsteps, float *out_u, int32_t out_on_device)
 {
     if (!h) return fail(STENCIL_EINVAL, "null plan");
+    TraceRange tr("stencil_run");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
     int rc = p->enqueue(nsteps);

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 #include "stencil.h"
 
@@ -20,6 +22,16 @@ stencil_tile default_tile(int R, int storage, int nx, int ny, int nz);
 int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz);
 int check_tile(int R, int storage, const stencil_tile &t);
 extern thread_local std::string g_last_error;
+
+// NVTX range for the lifetime of a scope (host-side phases: plan set-up,
+// step enqueue, tile selection, engine iterations); free when no profiler
+// is attached.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Row-by-row copy between pitched layouts; one flat copy when both sides
 // are dense (a 2D copy of many short rows is much slower than a flat one).

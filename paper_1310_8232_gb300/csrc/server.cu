@@ -158,6 +158,7 @@ int Server::read_back(Plan *p, float *out)
 
 void Server::finish(Request *r, int status)
 {
+    TraceRange tr("retire shot");
     const auto f0 = Clock::now();
     int rc = status;
     if (r->plan) {
@@ -227,6 +228,7 @@ void Server::run()
         }
 
         // ---- admission (plans made on the admission stream) ----------------
+        TraceRange tr_it("engine iteration");
         std::vector<Request *> admit;
         {
             std::unique_lock<std::mutex> lock(mu);

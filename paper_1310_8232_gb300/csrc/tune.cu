@@ -290,6 +290,7 @@ static int time_full(const Plan *p, Streams &S, const Cand &c, int nI, double *m
 
 int tune_plan(Plan *p, const stencil_desc *d)
 {
+    TraceRange tr("tile selection");
     const auto t_start = std::chrono::steady_clock::now();
     const int mode = d->tune_mode;
     const int P = d->tune.parts > 1 ? d->tune.parts : 5;
