@@ -59,8 +59,21 @@ def _compile(src: str, force: bool, newest: float, verbose: bool) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every csrc/*.cu and link libstencil.so; returns the library path."""
+    """Compile every csrc/*.cu and link libstencil.so; returns the library path.
+
+    Serialised across processes by a lock file, so ranks that start together
+    (one process per GPU) build once and the others find the library current."""
+    import fcntl
     os.makedirs(OBJDIR, exist_ok=True)
+    with open(os.path.join(OBJDIR, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     newest = _newest_dep()
     srcs = _sources()
     workers = max(1, min(len(srcs), os.cpu_count() or 1))
