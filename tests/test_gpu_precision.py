@@ -136,3 +136,60 @@ def test_512_layered_shot_errors_at_50_100_200_steps(env):
     assert table["fp16"][50] <= 5e-3 and table["fp16"][100] <= 5e-3
     assert table["fp16"][200] <= 2e-2          # regression bound; above the 5e-3 bar
     assert table["bf16"][100] <= 2e-1          # regression bound only
+
+
+def test_256_layered_shot_radius_4_errors(env):
+    """The 8th-order stencil with 16-bit storage: 256^3 layered model, 100
+    steps, relative L2 against the FP64 oracle."""
+    torch, st = env
+    n, R, T = 256, 4, 100
+    v = workloads.layered_velocity(n, n, n, seed=1310)
+    dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(v.max()))
+    ref, _ = oracle.run(v, workloads.DX, dt, R, T)
+    dv = torch.from_numpy(v).cuda()
+    dref = torch.from_numpy(ref).cuda()
+    errs = {}
+    for name, storage in (("fp32", 0), ("fp16", 1), ("bf16", 2)):
+        plan = st.stencil_plan(st.make_desc(dv, dt, radius=R, storage=storage, graph_steps=10,
+                                            stream=stream(torch)))
+        try:
+            st.stencil_step(plan, T)
+            errs[name] = st.stencil_rel_l2(plan, dref)
+        finally:
+            st.stencil_destroy(plan)
+    print(f"\nrelative L2 vs FP64 oracle, 256^3 layered, R=4, 100 steps: {errs}")
+    assert errs["fp32"] <= 1e-5
+    assert errs["fp16"] <= 5e-3
+    assert errs["bf16"] <= 2e-1
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_energy_with_16bit_storage(env, storage):
+    """The fused energy sum with 16-bit storage against the oracle's energy of
+    the stored (rounded) fields: equal within the storage's rounding."""
+    torch, st = env
+    nx, ny, nz, R = 48, 40, 36, 5
+    v = workloads.layered_velocity(nx, ny, nz, seed=81)
+    dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
+    u0 = workloads.gaussian_bump(nx, ny, nz, width=3.0)
+    plan = st.stencil_plan(st.make_desc(v, dt, radius=R, amp=0.0, storage=storage, stream=stream(torch)))
+    steps = 10
+    try:
+        st.stencil_set_fields(plan, u0, u0, 0)
+        st.stencil_record_start(plan, energy=True, capacity=steps)
+        prev = np.empty_like(v)
+        st.stencil_get_field(plan, 0, prev)
+        want = []
+        for _ in range(steps):
+            st.stencil_step(plan, 1)
+            u = np.empty_like(v)
+            st.stencil_get_field(plan, 0, u)
+            want.append(oracle.energy(v, workloads.DX, dt, R, u, prev))
+            prev = u
+        got = np.empty(steps)
+        assert st.stencil_record_read(plan, energy=got) == steps
+    finally:
+        st.stencil_destroy(plan)
+    want = np.array(want)
+    tol = 2.0 ** -9 if storage == 1 else 2.0 ** -6
+    assert np.all(np.abs(got - want) <= tol * np.abs(want)), np.max(np.abs(got - want) / np.abs(want))
