@@ -104,6 +104,9 @@ struct TiledShape {
     static constexpr int ROWS = 2;                      // rows per thread
     static constexpr int NT = TPR * TY / ROWS;          // threads per block
     static constexpr int RING = R + 1;                  // register ring of (u, partial) per plane
+    // ring slot chosen at run time (16-bit: the unrolled body outgrows the
+    // instruction cache); FP32 keeps the fully unrolled ring
+    static constexpr bool SPLIT = !F32;
     static constexpr int SU = 4;                        // u stages: 1 being read + 3 in flight
     static constexpr int SA = 4;                        // u_prev / kappa stages
     static constexpr int ZMAX = F32 ? 0 : 256;          // largest z-chunk (16-bit: scale tables)
@@ -148,6 +151,21 @@ struct Unroll<N, N> {
     {
     }
 };
+
+// run-time index k -> f(integral_constant<K>) for the K == k, K = 0..N-1
+template <int N, class F>
+__device__ __forceinline__ void dispatch(int k, F &f)
+{
+    static_assert(N >= 1 && N <= 6, "ring sizes 1 .. 6");
+    switch (k) {
+    case 0: f(std::integral_constant<int, 0>{}); break;
+    case 1: if constexpr (N > 1) f(std::integral_constant<int, 1>{}); break;
+    case 2: if constexpr (N > 2) f(std::integral_constant<int, 2>{}); break;
+    case 3: if constexpr (N > 3) f(std::integral_constant<int, 3>{}); break;
+    case 4: if constexpr (N > 4) f(std::integral_constant<int, 4>{}); break;
+    default: if constexpr (N > 5) f(std::integral_constant<int, 5>{}); break;
+    }
+}
 
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
@@ -258,6 +276,10 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     const int src_row = p.src.y - gy0;                     // this thread's row holding the source, if any
     const bool src_here = p.src.on && (unsigned)src_row < (unsigned)S::ROWS && (unsigned)(p.src.x - gx) < 4u &&
                           p.src.z >= z0 && p.src.z < z1;
+    // the source term of this step, w(n dt) scaled (one value for the whole
+    // launch: evaluated once, outside the unrolled plane loop)
+    float src_add = 0.0f;
+    if (src_here) src_add = (float)(p.src.scale * ricker(p.src.f, p.src.t0, (double)n_level * p.src.dt));
 
     // ring slot j holds, per row, plane i's u values and output i's partial
     // sum for the planes i with i mod RING == j (i counts planes from z0 - R)
@@ -275,33 +297,246 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     const float2 two = make_float2(2.0f, 2.0f);
     const float2 neg1 = make_float2(-1.0f, -1.0f);
     const float2 c0x3 = make_float2(3.0f * wf<R>(0), 3.0f * wf<R>(0));
-    int su_stage = 0, su_phase = 0;         // stage / parity of plane i
-    int sa_stage = 0, sa_phase = 0;         // aux stage / parity of output ja = i - 2R
     int done = 0;                           // planes fully processed (block-uniform)
 
-    for (int i0 = 0; i0 < nin; i0 += S::RING) {
-        float2 ekin = make_float2(0.f, 0.f);    // REC: energy terms of this group of RING planes
+    if constexpr (!S::SPLIT) {
+        int su_stage = 0, su_phase = 0;     // stage / parity of plane i
+        int sa_stage = 0, sa_phase = 0;     // aux stage / parity of output ja = i - 2R
+        for (int i0 = 0; i0 < nin; i0 += S::RING) {
+            float2 ekin = make_float2(0.f, 0.f);    // REC: energy terms of this group of RING planes
+            float2 epot = make_float2(0.f, 0.f);
+            auto body = [&](auto kc) {
+                constexpr int K = decltype(kc)::value;          // slot of plane i
+                const int i = i0 + K;
+                if (i >= nin) return;                           // block-uniform
+                if (!mbar_wait(&full_u[su_stage], su_phase, p.err, wait_limit)) *abort_flag = 1;
+                const E *pl = reinterpret_cast<const E *>(su + su_stage * S::U_STAGE) + own;
+                const float sgi = S::F32 ? 1.0f : sig_in[i];
+                // column of the thread's x group: rows -R .. ROWS-1+R around row 0
+                // (stored units; scaled to true values where they enter the sums)
+                float4 col[S::ROWS + 2 * R];
+#pragma unroll
+                for (int h = 0; h < S::ROWS; ++h) col[R + h] = ld4(pl + h * S::BW);
+                float2 nA[S::ROWS], nB[S::ROWS];
+#pragma unroll
+                for (int h = 0; h < S::ROWS; ++h) {
+                    nA[h] = make_float2(0.f, 0.f);
+                    nB[h] = make_float2(0.f, 0.f);
+                }
+                if (i >= R && i < R + nout) {
+                    // partial sums of output plane i: centre, x, y, and z below
+#pragma unroll
+                    for (int r = 1; r <= R; ++r) {
+                        col[R - r] = ld4(pl - r * S::BW);
+                        col[R + S::ROWS - 1 + r] = ld4(pl + (S::ROWS - 1 + r) * S::BW);
+                    }
+#pragma unroll
+                    for (int h = 0; h < S::ROWS; ++h) {
+                        const E *ph = pl + h * S::BW;
+                        const float4 c = col[R + h];
+                        float2 aA = __fmul2_rn(c0x3, lo2(c));
+                        float2 aB = __fmul2_rn(c0x3, hi2(c));
+                        float2 zA = make_float2(0.f, 0.f), zB = make_float2(0.f, 0.f);   // 16-bit: z terms
+                        // row[m] = u[gx - 8 + m], m = 0..19; own points are m = 8..11
+                        float row[20];
+                        {
+                            const float4 l1 = ld4(ph - 4);
+                            const float4 r1 = ld4(ph + 4);
+                            row[4] = l1.x; row[5] = l1.y; row[6] = l1.z; row[7] = l1.w;
+                            row[8] = c.x; row[9] = c.y; row[10] = c.z; row[11] = c.w;
+                            row[12] = r1.x; row[13] = r1.y; row[14] = r1.z; row[15] = r1.w;
+                            if constexpr (R > 4) {
+                                const float4 l2 = ld4(ph - 8);
+                                const float4 r2 = ld4(ph + 8);
+                                row[0] = l2.x; row[1] = l2.y; row[2] = l2.z; row[3] = l2.w;
+                                row[16] = r2.x; row[17] = r2.y; row[18] = r2.z; row[19] = r2.w;
+                            } else {
+                                row[0] = row[1] = row[2] = row[3] = 0.f;
+                                row[16] = row[17] = row[18] = row[19] = 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int r = 1; r <= R; ++r) {
+                            const float4 ym = col[R + h - r];
+                            const float4 yp = col[R + h + r];
+                            const float4 zm = uq[h][(K + S::RING - r) % S::RING];   // plane i - r (true values)
+                            float2 sA =
+                                __fadd2_rn(make_float2(row[8 - r], row[9 - r]), make_float2(row[8 + r], row[9 + r]));
+                            float2 sB =
+                                __fadd2_rn(make_float2(row[10 - r], row[11 - r]), make_float2(row[10 + r], row[11 + r]));
+                            sA = __fadd2_rn(sA, __fadd2_rn(lo2(ym), lo2(yp)));
+                            sB = __fadd2_rn(sB, __fadd2_rn(hi2(ym), hi2(yp)));
+                            const float2 cr = make_float2(wf<R>(r), wf<R>(r));
+                            if constexpr (S::F32) {
+                                sA = __fadd2_rn(sA, lo2(zm));
+                                sB = __fadd2_rn(sB, hi2(zm));
+                            } else {
+                                zA = __ffma2_rn(cr, lo2(zm), zA);
+                                zB = __ffma2_rn(cr, hi2(zm), zB);
+                            }
+                            aA = __ffma2_rn(cr, sA, aA);
+                            aB = __ffma2_rn(cr, sB, aB);
+                        }
+                        if constexpr (!S::F32) {
+                            // stored units -> true values: (x, y, centre) * s_n + z terms
+                            const float2 ss = make_float2(sgi, sgi);
+                            aA = __ffma2_rn(ss, aA, zA);
+                            aB = __ffma2_rn(ss, aB, zB);
+                        }
+                        nA[h] = aA;
+                        nB[h] = aB;
+                    }
+                }
+                if constexpr (!S::F32) {
+#pragma unroll
+                    for (int h = 0; h < S::ROWS; ++h) col[R + h] = scale4(col[R + h], sgi);
+                }
+                if (++su_stage == S::SU) {
+                    su_stage = 0;
+                    su_phase ^= 1;
+                }
+                // plane i is the z neighbour above outputs i-1 .. i-(R-1)
+#pragma unroll
+                for (int h = 0; h < S::ROWS; ++h) {
+                    const float4 c = col[R + h];
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        const float2 cr = make_float2(wf<R>(r), wf<R>(r));
+                        pa[h][(K + S::RING - r) % S::RING] = __ffma2_rn(cr, lo2(c), pa[h][(K + S::RING - r) % S::RING]);
+                        pb[h][(K + S::RING - r) % S::RING] = __ffma2_rn(cr, hi2(c), pb[h][(K + S::RING - r) % S::RING]);
+                    }
+                }
+                if (i >= 2 * R) {
+                    // ... and the last one above output i - R, which is now complete
+                    constexpr int KF = (K + 1) % S::RING;             // slot of plane i - R
+                    const float2 cR = make_float2(wf<R>(R), wf<R>(R));
+                    const int ja = i - 2 * R;
+                    if (!mbar_wait(&full_a[sa_stage], sa_phase, p.err, wait_limit)) *abort_flag = 1;
+                    const float sgp = S::F32 ? 1.0f : sig_prev[ja];
+                    float4 prev[S::ROWS], kap[S::ROWS];
+#pragma unroll
+                    for (int h = 0; h < S::ROWS; ++h) {
+                        prev[h] = ld4(reinterpret_cast<const E *>(sp + sa_stage * S::P_STAGE) + own_a + h * TX);
+                        if constexpr (!S::F32) prev[h] = scale4(prev[h], sgp);
+                        kap[h] = ld4(reinterpret_cast<const float *>(sk + sa_stage * S::K_STAGE) + own_a + h * TX);
+                    }
+                    if (++sa_stage == S::SA) {
+                        sa_stage = 0;
+                        sa_phase ^= 1;
+                    }
+                    const int o = z0 + ja;
+                    const float inv_out = S::F32 ? 1.0f : 1.0f / sig_out[ja];   // exact: a power of two
+                    float omax = 0.0f;
+#pragma unroll
+                    for (int h = 0; h < S::ROWS; ++h) {
+                        const float4 c = col[R + h];
+                        const float2 fA = __ffma2_rn(cR, lo2(c), pa[h][KF]);
+                        const float2 fB = __ffma2_rn(cR, hi2(c), pb[h][KF]);
+                        const float4 cc = uq[h][KF];
+                        // u^{n+1} = kappa * Lambda + (2 u^n - u^{n-1})
+                        const float2 oA =
+                            __ffma2_rn(lo2(kap[h]), fA, __ffma2_rn(neg1, lo2(prev[h]), __fmul2_rn(two, lo2(cc))));
+                        const float2 oB =
+                            __ffma2_rn(hi2(kap[h]), fB, __ffma2_rn(neg1, hi2(prev[h]), __fmul2_rn(two, hi2(cc))));
+                        float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
+                        if (src_here && src_row == h && o == p.src.z) {
+                            const int k = p.src.x - gx;
+                            if (k == 0) nxt.x += src_add;
+                            else if (k == 1) nxt.y += src_add;
+                            else if (k == 2) nxt.z += src_add;
+                            else nxt.w += src_add;
+                        }
+                        const bool ok = x_ok && gy0 + h < p.ny;
+                        if (REC && p.energy_on && ok) {
+                            // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa (into ekin) and
+                            // u^{n+1} Lambda(u^n) (into epot); points beyond nx count zero
+                            float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
+                            float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
+                            float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
+                            if (gx + 4 > p.nx) {
+                                const int nv = p.nx - gx;     // 1 .. 3
+                                if (nv < 2) uA.y = dA.y = 0.f;
+                                if (nv < 3) uB.x = dB.x = 0.f;
+                                uB.y = dB.y = 0.f;
+                            }
+                            const float2 rA = make_float2(rcp_approx(kap[h].x), rcp_approx(kap[h].y));
+                            const float2 rB = make_float2(rcp_approx(kap[h].z), rcp_approx(kap[h].w));
+                            ekin = __ffma2_rn(__fmul2_rn(dA, dA), rA, ekin);
+                            ekin = __ffma2_rn(__fmul2_rn(dB, dB), rB, ekin);
+                            epot = __ffma2_rn(uA, fA, epot);
+                            epot = __ffma2_rn(uB, fB, epot);
+                        }
+                        if constexpr (!S::F32) {
+                            if (ok)
+                                omax = fmaxf(omax, fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)),
+                                                         fmaxf(fabsf(nxt.z), fabsf(nxt.w))));
+                            nxt = scale4(nxt, inv_out);
+                        }
+                        if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
+                    }
+                    if constexpr (!S::F32) {
+                        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
+                        if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
+                    }
+
+                }
+                // slot K held plane i - R - 1, which nothing needs any more
+#pragma unroll
+                for (int h = 0; h < S::ROWS; ++h) {
+                    uq[h][K] = col[R + h];
+                    pa[h][K] = nA[h];
+                    pb[h][K] = nB[h];
+                }
+                // every thread is done with plane i's u stage and output (i-2R)'s
+                // aux stage: refill them
+                __syncthreads();
+                done = i + 1;
+                if (*abort_flag) {
+                    i0 = nin;                                    // block-uniform exit
+                    return;
+                }
+                if (tid == 0) {
+                    if (i + S::SU < nin) issue_u(i + S::SU);
+                    if (i >= 2 * R && i - 2 * R + S::SA < nout) issue_a(i - 2 * R + S::SA);
+                    if constexpr (!S::F32) {
+                        if (i >= 2 * R) {
+                            unsigned m = 0;
+                            for (int w = 0; w < S::NT / 32; ++w) m = max(m, wmax[(i & 1) * (S::NT / 32) + w]);
+                            if (m) atomicMax(p.amax + (int64_t)slot_out * p.nz + z0 + (i - 2 * R), m);
+                        }
+                    }
+                }
+            };
+            Unroll<0, S::RING>::run(body);
+            if (REC && p.energy_on) {
+                // the warp's FP32 sum over these planes, added in FP64 by lane 0
+                float e = (ekin.x + ekin.y) - (epot.x + epot.y);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+                if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
+            }
+        }
+    } else {
+        // The same per-plane work with the ring slot chosen at run time.  The
+        // shared-memory reads, the 16-bit conversions and the centre, x and y
+        // sums do not depend on the slot and are emitted once; only the parts
+        // that name ring registers (z terms, the completed output, the ring
+        // store) are instantiated per slot.  The loop body stays a fraction
+        // of the fully unrolled one, which keeps the instruction fetch ahead.
+        float2 ekin = make_float2(0.f, 0.f);        // REC: energy terms of the current group of RING planes
         float2 epot = make_float2(0.f, 0.f);
-        auto body = [&](auto kc) {
-            constexpr int K = decltype(kc)::value;          // slot of plane i
-            const int i = i0 + K;
-            if (i >= nin) return;                           // block-uniform
-            if (!mbar_wait(&full_u[su_stage], su_phase, p.err, wait_limit)) *abort_flag = 1;
-            const E *pl = reinterpret_cast<const E *>(su + su_stage * S::U_STAGE) + own;
+        int k = 0;                                  // ring slot of plane i (i mod RING)
+        static_assert(S::SU == 4 && S::SA == 4, "stage and parity from the plane index bits");
+        for (int i = 0; i < nin; ++i) {
+            if (!mbar_wait(&full_u[i & 3], (i >> 2) & 1, p.err, wait_limit)) *abort_flag = 1;
+            const E *pl = reinterpret_cast<const E *>(su + (i & 3) * S::U_STAGE) + own;
             const float sgi = S::F32 ? 1.0f : sig_in[i];
-            // column of the thread's x group: rows -R .. ROWS-1+R around row 0
-            // (stored units; scaled to true values where they enter the sums)
             float4 col[S::ROWS + 2 * R];
 #pragma unroll
             for (int h = 0; h < S::ROWS; ++h) col[R + h] = ld4(pl + h * S::BW);
-            float2 nA[S::ROWS], nB[S::ROWS];
-#pragma unroll
-            for (int h = 0; h < S::ROWS; ++h) {
-                nA[h] = make_float2(0.f, 0.f);
-                nB[h] = make_float2(0.f, 0.f);
-            }
-            if (i >= R && i < R + nout) {
-                // partial sums of output plane i: centre, x, y, and z below
+            const bool has_out = i >= R && i < R + nout;
+            float2 xA[S::ROWS], xB[S::ROWS];        // centre, x and y terms of output i (stored units)
+            if (has_out) {
 #pragma unroll
                 for (int r = 1; r <= R; ++r) {
                     col[R - r] = ld4(pl - r * S::BW);
@@ -313,9 +548,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     const float4 c = col[R + h];
                     float2 aA = __fmul2_rn(c0x3, lo2(c));
                     float2 aB = __fmul2_rn(c0x3, hi2(c));
-                    float2 zA = make_float2(0.f, 0.f), zB = make_float2(0.f, 0.f);   // 16-bit: z terms
-                    // row[m] = u[gx - 8 + m], m = 0..19; own points are m = 8..11
-                    float row[20];
+                    float row[20];                  // row[m] = u[gx - 8 + m]; own points m = 8..11
                     {
                         const float4 l1 = ld4(ph - 4);
                         const float4 r1 = ld4(ph + 4);
@@ -336,163 +569,167 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     for (int r = 1; r <= R; ++r) {
                         const float4 ym = col[R + h - r];
                         const float4 yp = col[R + h + r];
-                        const float4 zm = uq[h][(K + S::RING - r) % S::RING];   // plane i - r (true values)
-                        float2 sA =
-                            __fadd2_rn(make_float2(row[8 - r], row[9 - r]), make_float2(row[8 + r], row[9 + r]));
-                        float2 sB =
-                            __fadd2_rn(make_float2(row[10 - r], row[11 - r]), make_float2(row[10 + r], row[11 + r]));
+                        float2 sA, sB;
+                        if (r % 2 == 0) {
+                            sA = __fadd2_rn(make_float2(row[8 - r], row[9 - r]), make_float2(row[8 + r], row[9 + r]));
+                            sB = __fadd2_rn(make_float2(row[10 - r], row[11 - r]),
+                                            make_float2(row[10 + r], row[11 + r]));
+                        } else {
+                            // odd shifts pair values across register pairs: add them singly
+                            sA = make_float2(row[8 - r] + row[8 + r], row[9 - r] + row[9 + r]);
+                            sB = make_float2(row[10 - r] + row[10 + r], row[11 - r] + row[11 + r]);
+                        }
                         sA = __fadd2_rn(sA, __fadd2_rn(lo2(ym), lo2(yp)));
                         sB = __fadd2_rn(sB, __fadd2_rn(hi2(ym), hi2(yp)));
                         const float2 cr = make_float2(wf<R>(r), wf<R>(r));
-                        if constexpr (S::F32) {
-                            sA = __fadd2_rn(sA, lo2(zm));
-                            sB = __fadd2_rn(sB, hi2(zm));
-                        } else {
-                            zA = __ffma2_rn(cr, lo2(zm), zA);
-                            zB = __ffma2_rn(cr, hi2(zm), zB);
-                        }
                         aA = __ffma2_rn(cr, sA, aA);
                         aB = __ffma2_rn(cr, sB, aB);
                     }
-                    if constexpr (!S::F32) {
-                        // stored units -> true values: (x, y, centre) * s_n + z terms
-                        const float2 ss = make_float2(sgi, sgi);
-                        aA = __ffma2_rn(ss, aA, zA);
-                        aB = __ffma2_rn(ss, aB, zB);
-                    }
-                    nA[h] = aA;
-                    nB[h] = aB;
+                    xA[h] = aA;
+                    xB[h] = aB;
                 }
             }
             if constexpr (!S::F32) {
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) col[R + h] = scale4(col[R + h], sgi);
             }
-            if (++su_stage == S::SU) {
-                su_stage = 0;
-                su_phase ^= 1;
-            }
-            // plane i is the z neighbour above outputs i-1 .. i-(R-1)
-#pragma unroll
-            for (int h = 0; h < S::ROWS; ++h) {
-                const float4 c = col[R + h];
-#pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    const float2 cr = make_float2(wf<R>(r), wf<R>(r));
-                    pa[h][(K + S::RING - r) % S::RING] = __ffma2_rn(cr, lo2(c), pa[h][(K + S::RING - r) % S::RING]);
-                    pb[h][(K + S::RING - r) % S::RING] = __ffma2_rn(cr, hi2(c), pb[h][(K + S::RING - r) % S::RING]);
-                }
-            }
-            if (i >= 2 * R) {
-                // ... and the last one above output i - R, which is now complete
-                constexpr int KF = (K + 1) % S::RING;             // slot of plane i - R
-                const float2 cR = make_float2(wf<R>(R), wf<R>(R));
+            // u^{n-1} and kappa of output i - R, completed by this plane
+            const bool fin = i >= 2 * R;
+            const E *aux_p = nullptr;
+            const float *aux_k = nullptr;
+            float sgp = 1.0f, inv_out = 1.0f;
+            int o = 0;
+            if (fin) {
                 const int ja = i - 2 * R;
-                if (!mbar_wait(&full_a[sa_stage], sa_phase, p.err, wait_limit)) *abort_flag = 1;
-                const float sgp = S::F32 ? 1.0f : sig_prev[ja];
-                float4 prev[S::ROWS], kap[S::ROWS];
-#pragma unroll
-                for (int h = 0; h < S::ROWS; ++h) {
-                    prev[h] = ld4(reinterpret_cast<const E *>(sp + sa_stage * S::P_STAGE) + own_a + h * TX);
-                    if constexpr (!S::F32) prev[h] = scale4(prev[h], sgp);
-                    kap[h] = ld4(reinterpret_cast<const float *>(sk + sa_stage * S::K_STAGE) + own_a + h * TX);
-                }
-                if (++sa_stage == S::SA) {
-                    sa_stage = 0;
-                    sa_phase ^= 1;
-                }
-                const int o = z0 + ja;
-                const float inv_out = S::F32 ? 1.0f : 1.0f / sig_out[ja];   // exact: a power of two
-                float omax = 0.0f;
-#pragma unroll
-                for (int h = 0; h < S::ROWS; ++h) {
-                    const float4 c = col[R + h];
-                    const float2 fA = __ffma2_rn(cR, lo2(c), pa[h][KF]);
-                    const float2 fB = __ffma2_rn(cR, hi2(c), pb[h][KF]);
-                    const float4 cc = uq[h][KF];
-                    // u^{n+1} = kappa * Lambda + (2 u^n - u^{n-1})
-                    const float2 oA =
-                        __ffma2_rn(lo2(kap[h]), fA, __ffma2_rn(neg1, lo2(prev[h]), __fmul2_rn(two, lo2(cc))));
-                    const float2 oB =
-                        __ffma2_rn(hi2(kap[h]), fB, __ffma2_rn(neg1, hi2(prev[h]), __fmul2_rn(two, hi2(cc))));
-                    float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
-                    if (src_here && src_row == h && o == p.src.z) {
-                        const double t = (double)n_level * p.src.dt;
-                        const float add = (float)(p.src.scale * ricker(p.src.f, p.src.t0, t));
-                        const int k = p.src.x - gx;
-                        if (k == 0) nxt.x += add;
-                        else if (k == 1) nxt.y += add;
-                        else if (k == 2) nxt.z += add;
-                        else nxt.w += add;
-                    }
-                    const bool ok = x_ok && gy0 + h < p.ny;
-                    if (REC && p.energy_on && ok) {
-                        // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa (into ekin) and
-                        // u^{n+1} Lambda(u^n) (into epot); points beyond nx count zero
-                        float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
-                        float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
-                        float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
-                        if (gx + 4 > p.nx) {
-                            const int nv = p.nx - gx;     // 1 .. 3
-                            if (nv < 2) uA.y = dA.y = 0.f;
-                            if (nv < 3) uB.x = dB.x = 0.f;
-                            uB.y = dB.y = 0.f;
-                        }
-                        const float2 rA = make_float2(rcp_approx(kap[h].x), rcp_approx(kap[h].y));
-                        const float2 rB = make_float2(rcp_approx(kap[h].z), rcp_approx(kap[h].w));
-                        ekin = __ffma2_rn(__fmul2_rn(dA, dA), rA, ekin);
-                        ekin = __ffma2_rn(__fmul2_rn(dB, dB), rB, ekin);
-                        epot = __ffma2_rn(uA, fA, epot);
-                        epot = __ffma2_rn(uB, fB, epot);
-                    }
-                    if constexpr (!S::F32) {
-                        if (ok)
-                            omax = fmaxf(omax, fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)),
-                                                     fmaxf(fabsf(nxt.z), fabsf(nxt.w))));
-                        nxt = scale4(nxt, inv_out);
-                    }
-                    if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
-                }
+                if (!mbar_wait(&full_a[ja & 3], (ja >> 2) & 1, p.err, wait_limit)) *abort_flag = 1;
+                aux_p = reinterpret_cast<const E *>(sp + (ja & 3) * S::P_STAGE) + own_a;
+                aux_k = reinterpret_cast<const float *>(sk + (ja & 3) * S::K_STAGE) + own_a;
                 if constexpr (!S::F32) {
+                    sgp = sig_prev[ja];
+                    inv_out = 1.0f / sig_out[ja];   // exact: a power of two
+                }
+                o = z0 + ja;
+            }
+            const bool src_plane = src_here && o == p.src.z && fin;   // this thread adds the source now
+            float omax = 0.0f;
+            auto ring = [&](auto kc) {
+                constexpr int K = decltype(kc)::value;          // slot of plane i
+                constexpr int KF = (K + 1) % S::RING;           // slot of plane i - R
+                const float2 ss = make_float2(sgi, sgi);
+#pragma unroll
+                for (int h = 0; h < S::ROWS; ++h) {
+                    // plane i is the z neighbour above outputs i-1 .. i-(R-1)
+                    const float4 c = col[R + h];
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        const float2 cr = make_float2(wf<R>(r), wf<R>(r));
+                        pa[h][(K + S::RING - r) % S::RING] =
+                            __ffma2_rn(cr, lo2(c), pa[h][(K + S::RING - r) % S::RING]);
+                        pb[h][(K + S::RING - r) % S::RING] =
+                            __ffma2_rn(cr, hi2(c), pb[h][(K + S::RING - r) % S::RING]);
+                    }
+                    if (fin) {
+                        // ... and the last one above output i - R, which is now complete
+                        const float2 cR = make_float2(wf<R>(R), wf<R>(R));
+                        const float2 fA = __ffma2_rn(cR, lo2(c), pa[h][KF]);
+                        const float2 fB = __ffma2_rn(cR, hi2(c), pb[h][KF]);
+                        const float4 cc = uq[h][KF];
+                        float4 prev = ld4(aux_p + h * TX);
+                        if constexpr (!S::F32) prev = scale4(prev, sgp);
+                        const float4 kap = ld4(aux_k + h * TX);
+                        // u^{n+1} = kappa * Lambda + (2 u^n - u^{n-1})
+                        const float2 oA =
+                            __ffma2_rn(lo2(kap), fA, __ffma2_rn(neg1, lo2(prev), __fmul2_rn(two, lo2(cc))));
+                        const float2 oB =
+                            __ffma2_rn(hi2(kap), fB, __ffma2_rn(neg1, hi2(prev), __fmul2_rn(two, hi2(cc))));
+                        float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
+                        if (src_plane && src_row == h) {
+                            const int q = p.src.x - gx;
+                            if (q == 0) nxt.x += src_add;
+                            else if (q == 1) nxt.y += src_add;
+                            else if (q == 2) nxt.z += src_add;
+                            else nxt.w += src_add;
+                        }
+                        const bool ok = x_ok && gy0 + h < p.ny;
+                        if (REC && p.energy_on && ok) {
+                            float2 uA = lo2(nxt), uB = hi2(nxt);
+                            float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
+                            float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
+                            if (gx + 4 > p.nx) {
+                                const int nv = p.nx - gx;     // 1 .. 3
+                                if (nv < 2) uA.y = dA.y = 0.f;
+                                if (nv < 3) uB.x = dB.x = 0.f;
+                                uB.y = dB.y = 0.f;
+                            }
+                            const float2 rA = make_float2(rcp_approx(kap.x), rcp_approx(kap.y));
+                            const float2 rB = make_float2(rcp_approx(kap.z), rcp_approx(kap.w));
+                            ekin = __ffma2_rn(__fmul2_rn(dA, dA), rA, ekin);
+                            ekin = __ffma2_rn(__fmul2_rn(dB, dB), rB, ekin);
+                            epot = __ffma2_rn(uA, fA, epot);
+                            epot = __ffma2_rn(uB, fB, epot);
+                        }
+                        if constexpr (!S::F32) {
+                            const float m =
+                                fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)), fmaxf(fabsf(nxt.z), fabsf(nxt.w)));
+                            omax = fmaxf(omax, ok ? m : 0.0f);
+                            nxt = scale4(nxt, inv_out);
+                        }
+                        if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
+                    }
+                    // output i's partial: (centre, x, y) * s_n + z terms of
+                    // planes i-1 .. i-R; slot K held plane i - R - 1, now free
+                    if (has_out) {
+                        const float4 z1 = uq[h][(K + S::RING - 1) % S::RING];
+                        const float2 c1 = make_float2(wf<R>(1), wf<R>(1));
+                        float2 zA = __fmul2_rn(c1, lo2(z1)), zB = __fmul2_rn(c1, hi2(z1));
+#pragma unroll
+                        for (int r = 2; r <= R; ++r) {
+                            const float4 zm = uq[h][(K + S::RING - r) % S::RING];
+                            const float2 cr = make_float2(wf<R>(r), wf<R>(r));
+                            zA = __ffma2_rn(cr, lo2(zm), zA);
+                            zB = __ffma2_rn(cr, hi2(zm), zB);
+                        }
+                        pa[h][K] = __ffma2_rn(ss, xA[h], zA);
+                        pb[h][K] = __ffma2_rn(ss, xB[h], zB);
+                    } else {
+                        pa[h][K] = pb[h][K] = make_float2(0.f, 0.f);
+                    }
+                    uq[h][K] = c;
+                }
+            };
+            dispatch<S::RING>(k, ring);
+            if constexpr (!S::F32) {
+                if (fin) {
                     const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
                     if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
                 }
-
             }
-            // slot K held plane i - R - 1, which nothing needs any more
+            if (REC && p.energy_on && (k == S::RING - 1 || i == nin - 1)) {
+                // the warp's FP32 sum over the group's planes, added in FP64 by lane 0
+                float e = (ekin.x + ekin.y) - (epot.x + epot.y);
 #pragma unroll
-            for (int h = 0; h < S::ROWS; ++h) {
-                uq[h][K] = col[R + h];
-                pa[h][K] = nA[h];
-                pb[h][K] = nB[h];
+                for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+                if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
+                ekin = epot = make_float2(0.f, 0.f);
             }
+            if (++k == S::RING) k = 0;
             // every thread is done with plane i's u stage and output (i-2R)'s
             // aux stage: refill them
             __syncthreads();
             done = i + 1;
-            if (*abort_flag) {
-                i0 = nin;                                    // block-uniform exit
-                return;
-            }
+            if (*abort_flag) break;                 // block-uniform exit
             if (tid == 0) {
                 if (i + S::SU < nin) issue_u(i + S::SU);
-                if (i >= 2 * R && i - 2 * R + S::SA < nout) issue_a(i - 2 * R + S::SA);
-                if constexpr (!S::F32) {
-                    if (i >= 2 * R) {
-                        unsigned m = 0;
-                        for (int w = 0; w < S::NT / 32; ++w) m = max(m, wmax[(i & 1) * (S::NT / 32) + w]);
-                        if (m) atomicMax(p.amax + (int64_t)slot_out * p.nz + z0 + (i - 2 * R), m);
-                    }
+                if (fin && i - 2 * R + S::SA < nout) issue_a(i - 2 * R + S::SA);
+            }
+            if constexpr (!S::F32) {
+                // the plane's maximum, merged by the last warp (the first one issues the copies)
+                if (fin && tid == S::NT - 32) {
+                    unsigned m = 0;
+                    for (int w = 0; w < S::NT / 32; ++w) m = max(m, wmax[(i & 1) * (S::NT / 32) + w]);
+                    if (m) atomicMax(p.amax + (int64_t)slot_out * p.nz + z0 + (i - 2 * R), m);
                 }
             }
-        };
-        Unroll<0, S::RING>::run(body);
-        if (REC && p.energy_on) {
-            // the warp's FP32 sum over these planes, added in FP64 by lane 0
-            float e = (ekin.x + ekin.y) - (epot.x + epot.y);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-            if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
         }
     }
     if (*abort_flag && tid == 0) {
