@@ -69,6 +69,7 @@ def parse_args():
     ap.add_argument("--shots", type=int, default=64, help="batch: number of shots")
     ap.add_argument("--window", type=float, default=10.0, help="serve: arrival window (s)")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: mean arrivals per second")
+    ap.add_argument("--lanes", type=int, default=0, help="serve: size lanes of the shot server (0 = its default)")
     return ap.parse_args()
 
 
@@ -325,6 +326,9 @@ def run_serve(args, torch, st, workloads, ranks):
     cfg = st.shot_server_cfg_init()
     cfg.radius = R
     cfg.chunk_steps = 20
+    if args.lanes:
+        cfg.lanes = args.lanes
+    lanes = cfg.lanes
     server = st.shot_server_create(cfg)
     # every request's velocity model and output buffer are made before the
     # window opens (device models stay valid until admission), so the
@@ -360,7 +364,7 @@ def run_serve(args, torch, st, workloads, ranks):
         state, tm = st.shot_poll(server, t)
         if state != st.SHOT_DONE:
             continue
-        mine.append((tm.t_submit, tm.t_admit, tm.t_done, float(n) ** 3 * steps))
+        mine.append((tm.t_submit, tm.t_admit, tm.t_done, float(n) ** 3 * steps, n))
     st.shot_server_destroy(server)
     pooled = ranks.gather({"shots": mine, "stats": (stats.done, stats.failed, stats.iterations, stats.busy_s,
                                                     stats.admit_s, stats.build_s, stats.retire_s),
@@ -370,8 +374,10 @@ def run_serve(args, torch, st, workloads, ranks):
     # the ranks start together (barrier); the job spans the longest rank's
     # first-submit to last-done interval
     lat, queue_s, service, pts, span = [], [], [], 0.0, 0.0
+    by_size = {"side<128": [], "128<=side<203": [], "side>=203": []}
     for part in pooled:
-        for ts, ta, td, p in part["shots"]:
+        for ts, ta, td, p, n in part["shots"]:
+            by_size["side<128" if n ** 3 < 2 ** 21 else "128<=side<203" if n ** 3 < 2 ** 23 else "side>=203"].append(td - ts)
             lat.append(td - ts)
             queue_s.append(ta - ts)
             service.append(td - ta)
@@ -394,10 +400,13 @@ def run_serve(args, torch, st, workloads, ranks):
         "data": "synthetic",
         "config": {"workload": f"Poisson arrivals, mean {args.rate}/s over {args.window} s (seed 5020), "
                                f"cube side log-uniform 64-400, steps uniform 50-500, R={R}, "
-                               "8-layer random models, 80% HBM budget, 20 steps per engine iteration",
+                               "8-layer random models, 80% HBM budget, 20 steps per lane chunk, "
+                               f"{lanes} size lane(s)",
                    "shots": len(all_arrivals),
                    "parallelism": f"replicas: arrivals dealt round-robin to {ranks.env.world} shot server(s)"},
         "latency_s": {"p50": pct(lat_s, 0.50), "p99": pct(lat_s, 0.99), "mean": statistics.mean(lat) if lat else None},
+        "latency_by_size_s": {k: {"shots": len(v), "p50": pct(sorted(v), 0.50), "p99": pct(sorted(v), 0.99)}
+                              for k, v in by_size.items()},
         "queue_s": {"mean": statistics.mean(queue_s) if queue_s else None,
                     "p99": pct(sorted(queue_s), 0.99)},
         "service_s": {"mean": statistics.mean(service) if service else None},

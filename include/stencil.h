@@ -366,13 +366,18 @@ STENCIL_API int stencil_batch_destroy(stencil_batch_t b);
 
 /* A request loop for seismic shots arriving at any time.  One engine thread
  * admits queued shots in arrival order whenever a slot is free and the
- * shot's projected device bytes fit under the memory budget, keeps every
- * admitted shot's wavefields resident, and advances all resident shots
- * together, chunk_steps time steps per iteration, one launch per step over
- * all their tiles (the batch engine).  A shot that reaches its step count
- * retires: u^N is copied to its host buffer and its memory is freed.  Each
- * shot's result is exactly what stencil_run computes for it alone.  All
- * entry points are thread-safe. */
+ * shot's projected device bytes fit under the memory budget and keeps every
+ * admitted shot's wavefields resident.  Resident shots are split by size
+ * into `lanes`: lane k takes shots of [2^(19+2k), 2^(21+2k)) points per
+ * step (lane 0 everything below 2^21, the last lane everything above).  Each
+ * lane advances its shots together, chunk_steps time steps per chunk, one
+ * launch per step over all their tiles (the batch engine), on a stream of
+ * its own whose priority falls with the shot size; a lane starts its next
+ * chunk as soon as its last one ends, so small shots are not held to the
+ * step rate of large ones.  A shot that reaches its step count retires: u^N
+ * is copied to its host buffer and its memory is freed.  Each shot's result
+ * is exactly what stencil_run computes for it alone.  All entry points are
+ * thread-safe. */
 typedef struct shot_server_s *shot_server_t;
 
 typedef struct {
@@ -382,8 +387,10 @@ typedef struct {
     int32_t chunk_steps;        /* time steps per engine iteration (default 20) */
     int32_t radius;             /* every shot's radius (default 5) */
     int32_t storage;            /* every shot's storage (default FP32) */
-    void   *cuda_stream;        /* NULL = the server creates one */
+    void   *cuda_stream;        /* NULL = the server creates its lanes' streams; else one lane on it */
     stencil_tile tile;          /* tile shape (AUTO = 64 x 16) */
+    int32_t lanes;              /* size classes stepped independently, 1 .. 6 (default 3) */
+    int32_t pad;
 } shot_server_cfg;
 
 typedef enum { SHOT_QUEUED = 0, SHOT_RUNNING = 1, SHOT_DONE = 2, SHOT_FAILED = 3 } shot_state;

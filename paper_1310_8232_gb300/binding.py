@@ -109,6 +109,7 @@ class shot_server_cfg(ctypes.Structure):
         ("max_slots", ctypes.c_int32), ("chunk_steps", ctypes.c_int32),
         ("radius", ctypes.c_int32), ("storage", ctypes.c_int32),
         ("cuda_stream", ctypes.c_void_p), ("tile", stencil_tile),
+        ("lanes", ctypes.c_int32), ("pad", ctypes.c_int32),
     ]
 
 

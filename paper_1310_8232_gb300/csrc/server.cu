@@ -3,16 +3,21 @@
 // Requests (a problem description, a step count and a host output buffer)
 // arrive at any time through shot_submit.  One engine thread admits queued
 // shots in arrival order while a slot is free and the projected device bytes
-// fit under the memory budget, keeps every admitted shot's wavefields
-// resident, and advances all resident shots together, chunk_steps time steps
-// per iteration, with the grouped kernel (one launch per step over all
-// shots' tiles).  Each iteration launches the resident shots' steps first
-// and creates the newly admitted shots' plans on a second stream while the
-// GPU runs them; the new shots join at the next iteration.  Shots that reach their step count retire: the final field
-// is copied to the caller's buffer and the shot's memory is freed by a
-// second thread on its own stream (so the engine keeps stepping the other
-// shots meanwhile), and the slot goes to the next request.  Device memory
-// comes from a server-owned stream-ordered pool, so neither admission nor
+// fit under the memory budget, and keeps every admitted shot's wavefields
+// resident.  Resident shots are split by size (points per time step) into
+// lanes; each lane advances its shots together, chunk_steps time steps per
+// chunk, with the grouped kernel (one launch per step over all its shots'
+// tiles) on a stream of its own, the lanes of smaller shots on streams of
+// higher priority.  A lane starts its next chunk as soon as its previous one
+// has finished, independently of the other lanes, so a small shot is not
+// held to the step rate of the largest resident one, and the block scheduler
+// serves the small shots' blocks first while the large shots fill the rest
+// of the GPU.  New shots' plans are made on an admission stream while the
+// lanes run; a shot joins its lane when the lane's current chunk ends.
+// Shots that reach their step count retire: the final field is copied to the
+// caller's buffer and the shot's memory is freed by a second thread on its
+// own stream, and the slot goes to the next request.  Device memory comes
+// from a server-owned stream-ordered pool, so neither admission nor
 // retirement synchronises the whole device.  shot_poll reports state and
 // timing without blocking.
 #include <algorithm>
@@ -59,11 +64,32 @@ int64_t projected_bytes(const stencil_desc &d)
 
 }  // namespace
 
+// Shots of one size class, stepped together on one stream.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t done = nullptr;               // recorded after each chunk
+    Group group;
+    std::vector<Request *> resident;          // in the lane's group
+    std::vector<Request *> joining;           // admitted, join at the next chunk
+    bool rebuild = false;
+    bool in_flight = false;
+    int step_rc = STENCIL_OK;
+};
+
+// Lane of a shot: lane k holds shots of [2^(21+2(k-1)), 2^(21+2k)) points
+// (below 2 M points in lane 0; the last lane takes everything above).
+static int lane_of(const stencil_desc &d, int lanes)
+{
+    const int64_t points = (int64_t)d.nx * d.ny * d.nz;
+    int k = 0;
+    for (int64_t t = int64_t(1) << 21; k < lanes - 1 && points >= t; t <<= 2) ++k;
+    return k;
+}
+
 struct Server {
     shot_server_cfg cfg{};
     int dev = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
     cudaStream_t retire_stream = nullptr;
     cudaStream_t admit_stream = nullptr;      // plan creation, overlapping the engine's steps
     cudaMemPool_t pool = nullptr;
@@ -78,8 +104,8 @@ struct Server {
     bool stopping = false;
     shot_server_stats stats{};
 
-    std::vector<Request *> resident;      // engine thread only
-    Group group;
+    std::vector<std::unique_ptr<Lane>> lanes; // engine thread only (after creation)
+    uint64_t wake_seq = 0;                    // bumped (under mu) when a lane's chunk ends
     std::thread engine;
     int engine_error = STENCIL_OK;
 
@@ -92,12 +118,38 @@ struct Server {
     cudaEvent_t bounce_ev[2] = {nullptr, nullptr};
     int read_back(Plan *p, float *out);
 
+    ~Server();
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
     void run();
+    int launch_lane(Lane &L);                 // (re)describe the lane if needed, enqueue its next chunk
+    void end_chunk(Lane &L, int rc);          // account the finished chunk, retire finished shots
     void retire_loop();
     void retire(Request *r, int status);      // hand a shot to the retire thread
     void finish(Request *r, int status);      // retire thread: read back, free, report
 };
+
+// Everything the server holds on the device or host (the engine and retire
+// threads have ended, or never started); safe on a partly created server.
+Server::~Server()
+{
+    cudaSetDevice(dev);
+    for (auto &L : lanes) {
+        if (L->stream) cudaStreamSynchronize(L->stream);
+        L->group.release();
+        if (L->done) cudaEventDestroy(L->done);
+        if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
+    }
+    for (cudaStream_t st : {retire_stream, admit_stream}) {
+        if (!st) continue;
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (bounce[k]) cudaFreeHost(bounce[k]);
+        if (bounce_ev[k]) cudaEventDestroy(bounce_ev[k]);
+    }
+    if (pool) cudaMemPoolDestroy(pool);
+}
 
 void Server::retire(Request *r, int status)
 {
@@ -187,53 +239,109 @@ void Server::finish(Request *r, int status)
     cv.notify_all();
 }
 
+static void CUDART_CB wake_engine(void *arg)
+{
+    // host callback at the end of a lane's chunk: no CUDA calls here
+    Server *s = static_cast<Server *>(arg);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->wake_seq += 1;
+    }
+    s->cv.notify_all();
+}
+
+int Server::launch_lane(Lane &L)
+{
+    if (L.rebuild) {
+        const auto b0 = Clock::now();
+        std::vector<Plan *> plans;
+        std::vector<int64_t> n_end;
+        for (Request *r : L.resident) {
+            plans.push_back(r->plan);
+            n_end.push_back(r->nsteps);
+        }
+        L.group.zchunk = group_zchunk(L.group.R, L.group.storage, L.group.tx, L.group.ty, plans);
+        TiledInfo info{};
+        tiled_config(L.group.R, L.group.storage, L.group.tx, L.group.ty, &info);
+        if (info.zmax) L.group.zchunk = std::min(L.group.zchunk, info.zmax);
+        const int rc = L.group.build(plans, n_end);
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            stats.build_s += std::chrono::duration<double>(Clock::now() - b0).count();
+        }
+        if (rc) return rc;
+        L.rebuild = false;
+    }
+    L.step_rc = L.group.step(cfg.chunk_steps);
+    cudaError_t e = cudaEventRecord(L.done, L.stream);
+    if (e == cudaSuccess) e = cudaLaunchHostFunc(L.stream, wake_engine, this);
+    if (e != cudaSuccess && L.step_rc == STENCIL_OK) L.step_rc = fail_cuda(e, "lane chunk");
+    L.in_flight = true;
+    return STENCIL_OK;
+}
+
+void Server::end_chunk(Lane &L, int rc)
+{
+    std::vector<Request *> keep;
+    for (size_t i = 0; i < L.resident.size(); ++i) {
+        Request *r = L.resident[i];
+        Plan *p = r->plan;
+        const int pb = L.group.h_shots[i].parity_base;
+        p->steps_done = std::min<int64_t>(p->steps_done + cfg.chunk_steps, r->nsteps);
+        p->cur = (int)((p->steps_done + pb) & 1);
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            r->steps_done = p->steps_done;
+        }
+        if (rc != STENCIL_OK) {
+            retire(r, rc);
+            L.rebuild = true;
+        } else if (p->steps_done >= r->nsteps) {
+            retire(r, p->check_device_error());
+            L.rebuild = true;
+        } else {
+            keep.push_back(r);
+        }
+    }
+    L.resident.swap(keep);
+    L.in_flight = false;
+    std::lock_guard<std::mutex> lock(mu);
+    stats.iterations += 1;
+}
+
 void Server::run()
 {
     cudaSetDevice(dev);
-    bool rebuild = false;
+    int in_flight = 0;                        // lanes with a chunk on the GPU
+    Clock::time_point busy_t0{};
+    uint64_t seen_wake = 0;
     for (;;) {
-        // ---- this iteration's steps for the resident shots, launched first so
-        //      that admission below overlaps them ---------------------------
-        const bool stepping = !resident.empty();
-        auto it0 = Clock::now();
-        int rc = STENCIL_OK;
-        if (stepping) {
-            if (rebuild) {
-                std::vector<Plan *> plans;
-                std::vector<int64_t> n_end;
-                for (Request *r : resident) {
-                    plans.push_back(r->plan);
-                    n_end.push_back(r->nsteps);
-                }
-                group.zchunk = group_zchunk(group.R, group.storage, group.tx, group.ty, plans);
-                TiledInfo info{};
-                tiled_config(group.R, group.storage, group.tx, group.ty, &info);
-                if (info.zmax) group.zchunk = std::min(group.zchunk, info.zmax);
-                rc = group.build(plans, n_end);
-                if (rc) {
-                    engine_error = rc;
-                    for (Request *r : resident) retire(r, rc);
-                    resident.clear();
-                    continue;
-                }
-                rebuild = false;
-                const auto b1 = Clock::now();
-                {
-                    std::lock_guard<std::mutex> lock(mu);
-                    stats.build_s += std::chrono::duration<double>(b1 - it0).count();
-                }
-                it0 = b1;
+        // ---- every idle lane with shots starts its next chunk -------------
+        for (auto &lp : lanes) {
+            Lane &L = *lp;
+            if (L.in_flight) continue;
+            if (!L.joining.empty()) {
+                for (Request *r : L.joining) L.resident.push_back(r);
+                L.joining.clear();
+                L.rebuild = true;
             }
-            rc = group.step(cfg.chunk_steps);
+            if (L.resident.empty()) continue;
+            const int rc = launch_lane(L);
+            if (rc) {
+                engine_error = rc;
+                for (Request *r : L.resident) retire(r, rc);
+                L.resident.clear();
+                continue;
+            }
+            if (in_flight++ == 0) busy_t0 = Clock::now();
         }
 
         // ---- admission (plans made on the admission stream) ----------------
-        TraceRange tr_it("engine iteration");
+        int slots_used = 0;
+        for (auto &lp : lanes) slots_used += (int)(lp->resident.size() + lp->joining.size());
         std::vector<Request *> admit;
         {
             std::unique_lock<std::mutex> lock(mu);
-            if (!stepping)
-                cv.wait_for(lock, std::chrono::milliseconds(20), [&] { return stopping || !queue.empty(); });
             if (stopping) {
                 for (Request *r : queue) {
                     r->state = SHOT_FAILED;
@@ -243,12 +351,12 @@ void Server::run()
                     stats.failed += 1;
                 }
                 queue.clear();
-                if (!stepping) {
+                if (slots_used == 0 && in_flight == 0) {
                     cv.notify_all();
                     return;
                 }
             }
-            while (!queue.empty() && (int)(resident.size() + admit.size()) < cfg.max_slots &&
+            while (!queue.empty() && slots_used + (int)admit.size() < cfg.max_slots &&
                    stats.bytes_in_use + queue.front()->bytes <= budget) {
                 Request *r = queue.front();
                 queue.pop_front();
@@ -259,7 +367,7 @@ void Server::run()
                 admit.push_back(r);
             }
         }
-        std::vector<Request *> admitted;
+        TraceRange tr_it("engine iteration");
         for (Request *r : admit) {
             const auto a0 = Clock::now();
             stencil_desc d = r->desc;
@@ -268,7 +376,7 @@ void Server::run()
             d.graph_steps = 0;
             d.storage = cfg.storage;
             d.radius = cfg.radius;
-            d.tile = group.tx ? stencil_tile{STENCIL_KERNEL_TILED, group.tx, group.ty, -1} : d.tile;
+            d.tile = stencil_tile{STENCIL_KERNEL_TILED, lanes[0]->group.tx, lanes[0]->group.ty, -1};
             Plan *p = nullptr;
             const int arc = plan_create(&d, &p, pool);   // synchronous on the admission stream
             {
@@ -281,52 +389,48 @@ void Server::run()
                 retire(r, arc);
                 continue;
             }
-            p->stream = stream;                 // the group's stream from here on
+            Lane &L = *lanes[lane_of(r->desc, (int)lanes.size())];
+            p->stream = L.stream;               // the lane's stream from here on
             r->plan = p;
             r->velocity.clear();
             r->velocity.shrink_to_fit();
-            admitted.push_back(r);
+            L.joining.push_back(r);
         }
 
-        // ---- end of the iteration: shots that reached their count retire ----
-        if (stepping) {
-            cudaError_t e = cudaStreamSynchronize(stream);
-            if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "engine iteration");
-            {
+        // ---- lanes whose chunk has ended: account and retire ---------------
+        bool ended = false;
+        for (auto &lp : lanes) {
+            Lane &L = *lp;
+            if (!L.in_flight) continue;
+            const cudaError_t e = cudaEventQuery(L.done);
+            if (e == cudaErrorNotReady) continue;
+            int rc = L.step_rc;
+            if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "lane chunk");
+            end_chunk(L, rc);
+            ended = true;
+            if (--in_flight == 0) {
                 std::lock_guard<std::mutex> lock(mu);
-                stats.iterations += 1;
-                stats.busy_s += std::chrono::duration<double>(Clock::now() - it0).count();
+                stats.busy_s += std::chrono::duration<double>(Clock::now() - busy_t0).count();
             }
-            std::vector<Request *> keep;
-            for (size_t i = 0; i < resident.size(); ++i) {
-                Request *r = resident[i];
-                Plan *p = r->plan;
-                const int pb = group.h_shots[i].parity_base;
-                p->steps_done = std::min<int64_t>(p->steps_done + cfg.chunk_steps, r->nsteps);
-                p->cur = (int)((p->steps_done + pb) & 1);
-                {
-                    std::lock_guard<std::mutex> lock(mu);
-                    r->steps_done = p->steps_done;
-                }
-                if (rc != STENCIL_OK) {
-                    retire(r, rc);
-                    rebuild = true;
-                } else if (p->steps_done >= r->nsteps) {
-                    int drc = p->check_device_error();
-                    retire(r, drc);
-                    rebuild = true;
-                } else {
-                    keep.push_back(r);
-                }
-            }
-            resident.swap(keep);
         }
-        for (Request *r : admitted) resident.push_back(r);
-        if (!admitted.empty()) rebuild = true;
+        if (ended || !admit.empty()) continue;   // idle lanes may start at once
+
+        // ---- nothing to do until a chunk ends, a shot arrives or memory frees
+        int joining = 0;
+        for (auto &lp : lanes) joining += lp->in_flight ? 0 : (int)lp->joining.size();
+        if (joining) continue;
+        std::unique_lock<std::mutex> lock(mu);
+        cv.wait_for(lock, std::chrono::milliseconds(in_flight ? 2 : 20), [&] {
+            return (stopping && in_flight == 0) || wake_seq != seen_wake ||
+                   (!queue.empty() && slots_used < cfg.max_slots &&
+                    stats.bytes_in_use + queue.front()->bytes <= budget);
+        });
+        seen_wake = wake_seq;
     }
 }
 
 }  // namespace stencil
+
 
 using namespace stencil;
 
@@ -342,6 +446,7 @@ void shot_server_cfg_init(shot_server_cfg *c)
     c->radius = 5;
     c->storage = STENCIL_FP32;
     c->tile.kernel = STENCIL_KERNEL_AUTO;
+    c->lanes = 3;
 }
 
 int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
@@ -350,6 +455,7 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
     *out = nullptr;
     if (cfg->radius != 4 && cfg->radius != 5) return fail(STENCIL_EINVAL, "radius must be 4 or 5");
     if (cfg->max_slots < 1 || cfg->chunk_steps < 1) return fail(STENCIL_EINVAL, "max_slots, chunk_steps >= 1");
+    if (cfg->lanes < 1 || cfg->lanes > 6) return fail(STENCIL_EINVAL, "lanes must be 1 .. 6");
     if (!(cfg->hbm_budget_frac > 0) && cfg->hbm_budget_bytes <= 0)
         return fail(STENCIL_EINVAL, "need a memory budget");
     if (cfg->storage != STENCIL_FP32 && cfg->storage != STENCIL_FP16 && cfg->storage != STENCIL_BF16)
@@ -371,50 +477,47 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
     TiledInfo info;
     if (!tiled_config(cfg->radius, cfg->storage, t.tx, t.ty, &info))
         return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not built", t.tx, t.ty);
-    if (cfg->cuda_stream) {
-        s->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
-    } else {
-        if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess)
-            return fail_cuda(e, "cudaStreamCreate");
-        s->own_stream = true;
+    // lanes: one on the caller's stream, else cfg->lanes on streams of
+    // decreasing priority (lane 0, the smallest shots, highest)
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    const int nl = cfg->cuda_stream ? 1 : cfg->lanes;
+    for (int k = 0; k < nl; ++k) {
+        auto L = std::make_unique<Lane>();
+        if (cfg->cuda_stream) {
+            L->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+        } else {
+            const int prio = std::min(prio_least, prio_greatest + k);
+            if ((e = cudaStreamCreateWithPriority(&L->stream, cudaStreamNonBlocking, prio)) != cudaSuccess)
+                return fail_cuda(e, "cudaStreamCreateWithPriority");
+            L->own_stream = true;
+        }
+        if ((e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming)) != cudaSuccess) {
+            if (L->own_stream) cudaStreamDestroy(L->stream);
+            return fail_cuda(e, "cudaEventCreate");
+        }
+        L->group.R = cfg->radius;
+        L->group.storage = cfg->storage;
+        L->group.tx = t.tx;
+        L->group.ty = t.ty;
+        L->group.stream = L->stream;
+        L->group.graph_len = 0;
+        s->lanes.push_back(std::move(L));
     }
-    s->group.R = cfg->radius;
-    s->group.storage = cfg->storage;
-    s->group.tx = t.tx;
-    s->group.ty = t.ty;
-    s->group.stream = s->stream;
-    s->group.graph_len = 0;
-    if ((e = cudaStreamCreateWithFlags(&s->retire_stream, cudaStreamNonBlocking)) != cudaSuccess) {
-        if (s->own_stream) cudaStreamDestroy(s->stream);
+    if ((e = cudaStreamCreateWithFlags(&s->retire_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return fail_cuda(e, "cudaStreamCreate(retire)");
-    }
-    if ((e = cudaStreamCreateWithFlags(&s->admit_stream, cudaStreamNonBlocking)) != cudaSuccess) {
-        cudaStreamDestroy(s->retire_stream);
-        if (s->own_stream) cudaStreamDestroy(s->stream);
+    // admission sits on the path of every new shot: highest priority
+    if ((e = cudaStreamCreateWithPriority(&s->admit_stream, cudaStreamNonBlocking, prio_greatest)) != cudaSuccess)
         return fail_cuda(e, "cudaStreamCreate(admission)");
-    }
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.handleTypes = cudaMemHandleTypeNone;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = s->dev;
-    if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) {
-        cudaStreamDestroy(s->admit_stream);
-        cudaStreamDestroy(s->retire_stream);
-        if (s->own_stream) cudaStreamDestroy(s->stream);
-        return fail_cuda(e, "cudaMemPoolCreate");
-    }
+    if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) return fail_cuda(e, "cudaMemPoolCreate");
     for (int k = 0; k < 2; ++k) {
         if ((e = cudaMallocHost(reinterpret_cast<void **>(&s->bounce[k]), Server::BOUNCE_BYTES)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&s->bounce_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
-            for (int j = 0; j <= k; ++j) {
-                if (s->bounce[j]) cudaFreeHost(s->bounce[j]);
-                if (s->bounce_ev[j]) cudaEventDestroy(s->bounce_ev[j]);
-            }
-            cudaMemPoolDestroy(s->pool);
-            cudaStreamDestroy(s->admit_stream);
-            cudaStreamDestroy(s->retire_stream);
-            if (s->own_stream) cudaStreamDestroy(s->stream);
             return fail_cuda(e, "pinned read-back buffers");
         }
     }
@@ -533,20 +636,8 @@ int shot_server_destroy(shot_server_t h)
     }
     s->cv.notify_all();
     if (s->retirer.joinable()) s->retirer.join();
-    cudaSetDevice(s->dev);
-    s->group.release();
-    cudaStreamSynchronize(s->retire_stream);
-    cudaStreamDestroy(s->retire_stream);
-    cudaStreamSynchronize(s->admit_stream);
-    cudaStreamDestroy(s->admit_stream);
-    for (int k = 0; k < 2; ++k) {
-        if (s->bounce[k]) cudaFreeHost(s->bounce[k]);
-        if (s->bounce_ev[k]) cudaEventDestroy(s->bounce_ev[k]);
-    }
-    if (s->pool) cudaMemPoolDestroy(s->pool);
-    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     const int err = s->engine_error;
-    delete s;
+    delete s;                               // releases the streams, buffers and pool
     return err;
 }
 

@@ -64,6 +64,14 @@ def test_desc_init_defaults(st):
     assert d.tune.parts == 5 and d.graph_steps == 0
 
 
+def test_server_cfg_defaults(st):
+    c = st.shot_server_cfg_init()
+    assert c.hbm_budget_frac == 0.8 and c.max_slots == 64 and c.chunk_steps == 20
+    assert c.radius == 5 and c.storage == st.STENCIL_FP32 and c.lanes == 3 and not c.cuda_stream
+    import ctypes
+    assert ctypes.sizeof(c) == 64            # the C struct: 8 + 8 + 4 * 4 + 8 + 16 + 4 + 4 bytes
+
+
 def _desc(st, **kw):
     v = np.full((8, 8, 8), 2000.0, dtype=np.float32)
     d = st.make_desc(v, dt=1e-3, radius=4)

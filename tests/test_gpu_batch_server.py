@@ -198,3 +198,50 @@ def test_server_shot_with_invalid_model_fails_cleanly(env):
     finally:
         st.shot_server_destroy(server)
     assert np.array_equal(good, alone(env, v, dt, src, 10))
+
+
+# one shape per size lane of a three-lane server: below 2^21 points, 2^21 ..
+# 2^23, and above 2^23
+LANE_SHAPES = [(64, 64, 40), (160, 128, 120), (256, 160, 208)]
+
+
+@pytest.mark.parametrize("lanes", [1, 3])
+def test_server_lanes_results_identical_to_alone(env, lanes):
+    """Shots of all three size classes in the mix, arriving while others
+    run: with the lanes stepped independently (or all in one lane) every
+    result is bit-identical to the shot run alone."""
+    torch, st = env
+    server = make_server(st, chunk_steps=6, lanes=lanes)
+    jobs = []
+    try:
+        for i, (shape, steps) in enumerate(zip(LANE_SHAPES * 2, (31, 17, 9, 12, 25, 4))):
+            v, dt, src = shot(20 + i, shape)
+            out = np.full_like(v, np.nan)
+            t = st.shot_submit(server, st.make_desc(v, dt, radius=5, src=src), steps, out)
+            jobs.append((t, v, dt, src, steps, out))
+            time.sleep(0.001 * (i % 2))
+        for t, *_ in jobs:
+            assert st.shot_wait(server, t, 120.0) == st.SHOT_DONE
+        stats = st.shot_server_get_stats(server)
+        assert stats.done == len(jobs) and stats.failed == 0 and stats.bytes_in_use == 0
+        assert stats.iterations >= 1
+    finally:
+        st.shot_server_destroy(server)
+    for t, v, dt, src, steps, out in jobs:
+        assert np.array_equal(out, alone(env, v, dt, src, steps)), t
+
+
+def test_server_on_callers_stream_and_bad_lane_count(env):
+    torch, st = env
+    with pytest.raises(st.StencilError) as ei:
+        make_server(st, lanes=7)
+    assert ei.value.code == st.STENCIL_EINVAL
+    server = make_server(st, chunk_steps=4, cuda_stream=stream(torch))   # one lane, on the given stream
+    try:
+        v, dt, src = shot(30, (96, 64, 40))
+        out = np.empty_like(v)
+        t = st.shot_submit(server, st.make_desc(v, dt, radius=5, src=src), 10, out)
+        assert st.shot_wait(server, t, 60.0) == st.SHOT_DONE
+    finally:
+        st.shot_server_destroy(server)
+    assert np.array_equal(out, alone(env, v, dt, src, 10))
