@@ -417,7 +417,9 @@ STENCIL_API void shot_server_cfg_init(shot_server_cfg *cfg);
 STENCIL_API int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out);
 /* Queue a shot of nsteps time steps; u^N will be written to out_host (dense
  * nx*ny*nz floats, or NULL), which must stay valid until the shot is DONE or
- * FAILED.  A host velocity is copied at once; a device velocity must stay
+ * FAILED.  A page-locked out_host (cudaHostAlloc, cudaHostRegister) is
+ * written by one device-to-host copy, any other through the server's pinned
+ * bounce buffers.  A host velocity is copied at once; a device velocity must stay
  * valid until the shot is admitted.  STENCIL_EBUDGET if the shot alone
  * exceeds the budget (it is recorded as FAILED). */
 STENCIL_API int shot_submit(shot_server_t s, const stencil_desc *d, int32_t nsteps, float *out_host,

@@ -19,15 +19,17 @@ void Group::release()
     cap_shots = cap_items = 0;
 }
 
-int group_zchunk(int R, int storage, int tx, int ty, const std::vector<Plan *> &plans)
+int group_zchunk(int R, int storage, int tx, int ty, const std::vector<Plan *> &plans, double share)
 {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-    const int slots = sms * std::max(1, tiled_blocks_per_sm(R, storage, tx, ty));
+    const int slots = std::max(1, (int)(share * sms * std::max(1, tiled_blocks_per_sm(R, storage, tx, ty))));
     TiledInfo info{};
     tiled_config(R, storage, tx, ty, &info);
-    static const int cand[] = {16, 24, 32, 48, 64, 96, 128};
+    // the single-plan choice's candidates up to 128: small grids want short
+    // z-marches (latency), big groups fewer warm-up planes
+    static const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128};
     int best = 32;
     double best_t = -1;
     for (int zc : cand) {

@@ -30,7 +30,9 @@ struct Group {
     int step(int k);
 };
 
-// A common z-chunk for the blocks of several grids sharing the GPU.
-int group_zchunk(int R, int storage, int tx, int ty, const std::vector<Plan *> &plans);
+// A common z-chunk for the blocks of several grids sharing the GPU; `share`
+// is the fraction of the GPU's block slots the group can expect (1 when it
+// runs alone, less when other groups run beside it).
+int group_zchunk(int R, int storage, int tx, int ty, const std::vector<Plan *> &plans, double share = 1.0);
 
 }  // namespace stencil

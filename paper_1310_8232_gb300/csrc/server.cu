@@ -9,7 +9,8 @@
 // chunk, with the grouped kernel (one launch per step over all its shots'
 // tiles) on a stream of its own, the lanes of smaller shots on streams of
 // higher priority.  A lane starts its next chunk as soon as its previous one
-// has finished, independently of the other lanes, so a small shot is not
+// has finished (and queues it behind the running one when no shot can join
+// or leave in between), independently of the other lanes, so a small shot is not
 // held to the step rate of the largest resident one, and the block scheduler
 // serves the small shots' blocks first while the large shots fill the rest
 // of the GPU.  New shots' plans are made on an admission stream while the
@@ -68,13 +69,13 @@ int64_t projected_bytes(const stencil_desc &d)
 struct Lane {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaEvent_t done = nullptr;               // recorded after each chunk
+    cudaEvent_t done[2] = {nullptr, nullptr}; // recorded after each chunk (ring of the chunks in flight)
     Group group;
     std::vector<Request *> resident;          // in the lane's group
     std::vector<Request *> joining;           // admitted, join at the next chunk
     bool rebuild = false;
-    bool in_flight = false;
-    int step_rc = STENCIL_OK;
+    int head = 0, n_flight = 0;               // oldest chunk in flight, chunks in flight (0 .. 2)
+    int step_rc[2] = {STENCIL_OK, STENCIL_OK};
 };
 
 // Lane of a shot: lane k holds shots of [2^(21+2(k-1)), 2^(21+2k)) points
@@ -136,7 +137,8 @@ Server::~Server()
     for (auto &L : lanes) {
         if (L->stream) cudaStreamSynchronize(L->stream);
         L->group.release();
-        if (L->done) cudaEventDestroy(L->done);
+        for (cudaEvent_t ev : L->done)
+            if (ev) cudaEventDestroy(ev);
         if (L->own_stream && L->stream) cudaStreamDestroy(L->stream);
     }
     for (cudaStream_t st : {retire_stream, admit_stream}) {
@@ -174,9 +176,32 @@ void Server::retire_loop()
     }
 }
 
-// u^N of a finished shot into the caller's dense buffer, through the pinned
-// bounce halves (device-to-pinned copy of chunk k overlaps the host copy of
-// chunk k-1), so the read-back never takes the driver's pageable path.
+// Host copy of n bytes split over a few threads (one core copies ~14 GB/s,
+// far below the device-to-host link).
+static void parallel_copy(void *dst, const void *src, size_t n)
+{
+    constexpr size_t SLICE = 8u << 20;
+    const int parts = (int)std::min<size_t>(4, std::max<size_t>(1, n / SLICE));
+    if (parts == 1) {
+        std::memcpy(dst, src, n);
+        return;
+    }
+    const size_t per = (n / parts + 63) & ~size_t(63);
+    std::vector<std::thread> helpers;
+    for (int k = 1; k < parts; ++k) {
+        const size_t o = std::min(n, per * k), len = std::min(n, o + per) - o;
+        helpers.emplace_back([=] { std::memcpy(static_cast<char *>(dst) + o, static_cast<const char *>(src) + o, len); });
+    }
+    std::memcpy(dst, src, std::min(n, per));
+    for (auto &t : helpers) t.join();
+}
+
+// u^N of a finished shot into the caller's dense buffer.  A page-locked
+// buffer takes one device-to-host copy.  Any other goes through the pinned
+// bounce halves (the device-to-pinned copy of chunk k overlaps the host copy
+// of chunk k-1): a device-to-host copy straight into pageable memory that
+// the process has not touched yet faults its pages in one by one on the
+// driver's side, and measured an order of magnitude slower under load.
 int Server::read_back(Plan *p, float *out)
 {
     const float *src = nullptr;
@@ -184,18 +209,26 @@ int Server::read_back(Plan *p, float *out)
     if (rc) return rc;
     const size_t row_bytes = (size_t)p->nx * sizeof(float);
     const int64_t rows = (int64_t)p->ny * p->nz;
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeHost) {
+        cudaError_t e = memcpy_rows(out, row_bytes, src, p->pitch * sizeof(float), row_bytes, (size_t)rows,
+                                    cudaMemcpyDeviceToHost, retire_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(retire_stream);
+        return e == cudaSuccess ? STENCIL_OK : fail_cuda(e, "read-back");
+    }
+    cudaGetLastError();                         // an unregistered pointer is not an error here
     const int64_t per = std::max<int64_t>(1, (int64_t)(BOUNCE_BYTES / row_bytes));
     int64_t prev_r0 = -1, prev_n = 0;
     int k = 0;
     for (int64_t r0 = 0; r0 < rows; r0 += per, ++k) {
         const int64_t n = std::min(per, rows - r0);
         cudaError_t e = memcpy_rows(bounce[k & 1], row_bytes, src + r0 * p->pitch, p->pitch * sizeof(float),
-                                          row_bytes, (size_t)n, cudaMemcpyDeviceToHost, retire_stream);
+                                    row_bytes, (size_t)n, cudaMemcpyDeviceToHost, retire_stream);
         if (e == cudaSuccess) e = cudaEventRecord(bounce_ev[k & 1], retire_stream);
         if (e != cudaSuccess) return fail_cuda(e, "read-back");
         if (prev_r0 >= 0) {
             if ((e = cudaEventSynchronize(bounce_ev[(k - 1) & 1])) != cudaSuccess) return fail_cuda(e, "read-back");
-            std::memcpy(out + prev_r0 * p->nx, bounce[(k - 1) & 1], (size_t)prev_n * row_bytes);
+            parallel_copy(out + prev_r0 * p->nx, bounce[(k - 1) & 1], (size_t)prev_n * row_bytes);
         }
         prev_r0 = r0;
         prev_n = n;
@@ -203,7 +236,7 @@ int Server::read_back(Plan *p, float *out)
     if (prev_r0 >= 0) {
         cudaError_t e = cudaEventSynchronize(bounce_ev[(k - 1) & 1]);
         if (e != cudaSuccess) return fail_cuda(e, "read-back");
-        std::memcpy(out + prev_r0 * p->nx, bounce[(k - 1) & 1], (size_t)prev_n * row_bytes);
+        parallel_copy(out + prev_r0 * p->nx, bounce[(k - 1) & 1], (size_t)prev_n * row_bytes);
     }
     return STENCIL_OK;
 }
@@ -260,7 +293,11 @@ int Server::launch_lane(Lane &L)
             plans.push_back(r->plan);
             n_end.push_back(r->nsteps);
         }
-        L.group.zchunk = group_zchunk(L.group.R, L.group.storage, L.group.tx, L.group.ty, plans);
+        // the lanes with shots share the GPU's block slots
+        int active = 0;
+        for (auto &lp : lanes) active += !lp->resident.empty() || !lp->joining.empty();
+        L.group.zchunk = group_zchunk(L.group.R, L.group.storage, L.group.tx, L.group.ty, plans,
+                                      1.0 / std::max(1, active));
         TiledInfo info{};
         tiled_config(L.group.R, L.group.storage, L.group.tx, L.group.ty, &info);
         if (info.zmax) L.group.zchunk = std::min(L.group.zchunk, info.zmax);
@@ -272,16 +309,22 @@ int Server::launch_lane(Lane &L)
         if (rc) return rc;
         L.rebuild = false;
     }
-    L.step_rc = L.group.step(cfg.chunk_steps);
-    cudaError_t e = cudaEventRecord(L.done, L.stream);
+    const int k = (L.head + L.n_flight) & 1;
+    L.step_rc[k] = L.group.step(cfg.chunk_steps);
+    cudaError_t e = cudaEventRecord(L.done[k], L.stream);
     if (e == cudaSuccess) e = cudaLaunchHostFunc(L.stream, wake_engine, this);
-    if (e != cudaSuccess && L.step_rc == STENCIL_OK) L.step_rc = fail_cuda(e, "lane chunk");
-    L.in_flight = true;
+    if (e != cudaSuccess && L.step_rc[k] == STENCIL_OK) L.step_rc[k] = fail_cuda(e, "lane chunk");
+    L.n_flight += 1;
     return STENCIL_OK;
 }
 
 void Server::end_chunk(Lane &L, int rc)
 {
+    if (rc != STENCIL_OK && L.n_flight > 1) {
+        // the chunk queued behind the failed one still uses the shots' memory
+        cudaStreamSynchronize(L.stream);
+        L.n_flight = 1;
+    }
     std::vector<Request *> keep;
     for (size_t i = 0; i < L.resident.size(); ++i) {
         Request *r = L.resident[i];
@@ -304,7 +347,8 @@ void Server::end_chunk(Lane &L, int rc)
         }
     }
     L.resident.swap(keep);
-    L.in_flight = false;
+    L.head ^= 1;
+    L.n_flight -= 1;
     std::lock_guard<std::mutex> lock(mu);
     stats.iterations += 1;
 }
@@ -316,24 +360,38 @@ void Server::run()
     Clock::time_point busy_t0{};
     uint64_t seen_wake = 0;
     for (;;) {
-        // ---- every idle lane with shots starts its next chunk -------------
+        // ---- every idle lane with shots starts its next chunk; a lane whose
+        //      membership cannot change before its running chunk ends queues
+        //      the chunk after it too, so the GPU does not wait for the host
         for (auto &lp : lanes) {
             Lane &L = *lp;
-            if (L.in_flight) continue;
-            if (!L.joining.empty()) {
-                for (Request *r : L.joining) L.resident.push_back(r);
-                L.joining.clear();
-                L.rebuild = true;
+            if (L.n_flight == 0) {
+                if (!L.joining.empty()) {
+                    for (Request *r : L.joining) L.resident.push_back(r);
+                    L.joining.clear();
+                    L.rebuild = true;
+                }
+                if (L.resident.empty()) continue;
+                const int rc = launch_lane(L);
+                if (rc) {
+                    engine_error = rc;
+                    for (Request *r : L.resident) retire(r, rc);
+                    L.resident.clear();
+                    continue;
+                }
             }
-            if (L.resident.empty()) continue;
-            const int rc = launch_lane(L);
-            if (rc) {
-                engine_error = rc;
-                for (Request *r : L.resident) retire(r, rc);
-                L.resident.clear();
-                continue;
+            if (L.n_flight == 1 && L.joining.empty() && !L.rebuild && L.step_rc[L.head] == STENCIL_OK) {
+                bool finishing = false;              // a shot ends within the running chunk
+                for (Request *r : L.resident) finishing |= r->plan->steps_done + cfg.chunk_steps >= r->nsteps;
+                if (!finishing) launch_lane(L);
             }
-            if (in_flight++ == 0) busy_t0 = Clock::now();
+        }
+
+        {
+            int busy_now = 0;
+            for (auto &lp : lanes) busy_now += lp->n_flight > 0;
+            if (in_flight == 0 && busy_now > 0) busy_t0 = Clock::now();
+            in_flight = busy_now;
         }
 
         // ---- admission (plans made on the admission stream) ----------------
@@ -401,23 +459,27 @@ void Server::run()
         bool ended = false;
         for (auto &lp : lanes) {
             Lane &L = *lp;
-            if (!L.in_flight) continue;
-            const cudaError_t e = cudaEventQuery(L.done);
-            if (e == cudaErrorNotReady) continue;
-            int rc = L.step_rc;
-            if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "lane chunk");
-            end_chunk(L, rc);
-            ended = true;
-            if (--in_flight == 0) {
-                std::lock_guard<std::mutex> lock(mu);
-                stats.busy_s += std::chrono::duration<double>(Clock::now() - busy_t0).count();
+            while (L.n_flight > 0) {
+                const cudaError_t e = cudaEventQuery(L.done[L.head]);
+                if (e == cudaErrorNotReady) break;
+                int rc = L.step_rc[L.head];
+                if (rc == STENCIL_OK && e != cudaSuccess) rc = fail_cuda(e, "lane chunk");
+                end_chunk(L, rc);
+                ended = true;
             }
         }
+        int busy_now = 0;
+        for (auto &lp : lanes) busy_now += lp->n_flight > 0;
+        if (in_flight > 0 && busy_now == 0) {
+            std::lock_guard<std::mutex> lock(mu);
+            stats.busy_s += std::chrono::duration<double>(Clock::now() - busy_t0).count();
+        }
+        in_flight = busy_now;
         if (ended || !admit.empty()) continue;   // idle lanes may start at once
 
         // ---- nothing to do until a chunk ends, a shot arrives or memory frees
         int joining = 0;
-        for (auto &lp : lanes) joining += lp->in_flight ? 0 : (int)lp->joining.size();
+        for (auto &lp : lanes) joining += lp->n_flight ? 0 : (int)lp->joining.size();
         if (joining) continue;
         std::unique_lock<std::mutex> lock(mu);
         cv.wait_for(lock, std::chrono::milliseconds(in_flight ? 2 : 20), [&] {
@@ -492,7 +554,9 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
                 return fail_cuda(e, "cudaStreamCreateWithPriority");
             L->own_stream = true;
         }
-        if ((e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming)) != cudaSuccess) {
+        if ((e = cudaEventCreateWithFlags(&L->done[0], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&L->done[1], cudaEventDisableTiming)) != cudaSuccess) {
+            if (L->done[0]) cudaEventDestroy(L->done[0]);
             if (L->own_stream) cudaStreamDestroy(L->stream);
             return fail_cuda(e, "cudaEventCreate");
         }
@@ -515,12 +579,10 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = s->dev;
     if ((e = cudaMemPoolCreate(&s->pool, &props)) != cudaSuccess) return fail_cuda(e, "cudaMemPoolCreate");
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2; ++k)
         if ((e = cudaMallocHost(reinterpret_cast<void **>(&s->bounce[k]), Server::BOUNCE_BYTES)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&s->bounce_ev[k], cudaEventDisableTiming)) != cudaSuccess) {
+            (e = cudaEventCreateWithFlags(&s->bounce_ev[k], cudaEventDisableTiming)) != cudaSuccess)
             return fail_cuda(e, "pinned read-back buffers");
-        }
-    }
     uint64_t keep = (uint64_t)s->budget;                 // keep freed memory for the next shots
     cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     s->stats.budget_bytes = s->budget;
