@@ -93,7 +93,31 @@ struct SweepParams {
     // makes that wait run out)
     uint32_t wait_ns;
     uint32_t fault_tx;
+    // absorbing layer folded into the sweep (FP32 tiled kernel; 0 = none):
+    // u^{n+1} = (plain update + eta u^{n-1}) / (1 + eta), eta = eta_max
+    // ((W-d)/W)^2 at distance d < W from the nearest face, taken as
+    // plain * g_d + u^{n-1} * h_d from the table absorb_tab[d] = (g_d, h_d) =
+    // (1/(1+eta), eta/(1+eta)), d = 0..W (entry W = (1, 0)); then the source
+    int32_t absorb_w;
+    const float2 *absorb_tab;
 };
+
+// The layer on 4 consecutive points (x = gx..gx+3) of row y, plane z.
+__device__ __forceinline__ void absorb4(int W, const float2 *tab, int nx, int ny, int nz, int gx, int y, int z,
+                                        float4 &v, const float4 &prev)
+{
+    const int dyz = min(min(z, nz - 1 - z), min(y, ny - 1 - y));
+    if (dyz >= W && gx >= W && gx + 3 <= nx - 1 - W) return;
+    float *pv = &v.x;
+    const float *pp = &prev.x;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        // x beyond nx (the row's padding) clamps to d = 0: written, never read
+        const int d = max(0, min(W, min(dyz, min(gx + j, nx - 1 - gx - j))));
+        const float2 t = tab[d];
+        pv[j] = fmaf(t.y, pp[j], pv[j] * t.x);
+    }
+}
 
 // A shot of a grouped launch: its tensor maps (by parity of the level),
 // buffers and parameters, in 64-byte aligned device memory.

@@ -41,7 +41,7 @@ struct StepOps {
     int32_t step_off;
     // absorbing layer: u^{n-1} of the layer's points saved before the sweep
     int32_t absorb_w;               // 0: none
-    float absorb_eta;
+    const float2 *absorb_tab;       // (g_d, h_d) = (1/(1+eta_d), eta_d/(1+eta_d)), d = 0..W
     int64_t shell_points;
     float *save;
     Source src;                     // added after the layer when absorb_w > 0

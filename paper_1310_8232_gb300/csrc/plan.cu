@@ -202,8 +202,13 @@ SweepParams Plan::params(int parity, int step_off) const
     s.rec_n0 = rec_n0;
     s.rec_cap = rec_cap;
     s.energy_on = rec_mem ? rec_energy_on : 0;
-    // with an absorbing layer the source is added after the layer's pass
-    if (absorb_w > 0) s.src.on = 0;
+    if (absorb_folded()) {
+        // the tiled FP32 sweep applies the layer itself, then the source
+        s.absorb_w = absorb_w;
+        s.absorb_tab = absorb_tab;
+    } else if (absorb_w > 0) {
+        s.src.on = 0;                       // added after the layer's own pass
+    }
     s.wait_ns = wait_ns;
     s.fault_tx = fault_tx;
     return s;
@@ -219,8 +224,8 @@ StepOps Plan::step_ops(int step_off) const
     o.plane = pitch * ny;
     o.step_base = d_step;
     o.step_off = step_off;
-    o.absorb_w = absorb_w;
-    o.absorb_eta = absorb_eta;
+    o.absorb_w = absorb_folded() ? 0 : absorb_w;
+    o.absorb_tab = absorb_tab;
     o.shell_points = absorb_shell;
     o.save = absorb_save;
     o.src = src;
@@ -240,7 +245,15 @@ StepOps Plan::step_ops(int step_off) const
     return o;
 }
 
-bool Plan::has_step_ops() const { return absorb_w > 0 || inj != nullptr || rec != nullptr; }
+bool Plan::absorb_folded() const
+{
+    return absorb_w > 0 && tile.kernel == STENCIL_KERNEL_TILED && storage == STENCIL_FP32;
+}
+
+bool Plan::has_step_ops() const
+{
+    return (absorb_w > 0 && !absorb_folded()) || inj != nullptr || rec != nullptr;
+}
 
 // One time step: [layer save] sweep [layer apply, source, injection, record]
 cudaError_t Plan::launch_one(int parity, int step_off, cudaStream_t s) const
@@ -670,9 +683,24 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     if (p->absorb_w > 0) {
         // u^{n-1} of the layer's points, saved before each sweep
         p->absorb_shell = shell_points(d->nx, d->ny, d->nz, p->absorb_w);
-        e = p->dev_alloc(reinterpret_cast<void **>(&p->absorb_save), sizeof(float) * (size_t)p->absorb_shell);
+        // ... and the damping factors by distance to the nearest face:
+        // g_d = 1/(1+eta_d), h_d = eta_d/(1+eta_d), eta_d = eta_max ((W-d)/W)^2
+        // (FP64, rounded once), entry W = (1, 0)
+        const size_t save_bytes = ((sizeof(float) * (size_t)p->absorb_shell + 15) / 16) * 16;
+        const size_t tab_n = (size_t)p->absorb_w + 1;
+        e = p->dev_alloc(reinterpret_cast<void **>(&p->absorb_save), save_bytes + sizeof(float2) * tab_n);
         if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(absorbing layer)"));
-        p->device_bytes += (int64_t)sizeof(float) * p->absorb_shell;
+        p->absorb_tab = reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(p->absorb_save) + save_bytes);
+        p->absorb_tab_host.resize(tab_n);
+        for (int dd = 0; dd <= p->absorb_w; ++dd) {
+            const double a = (double)(p->absorb_w - dd) / p->absorb_w;
+            const double eta = d->absorb_eta * a * a;
+            p->absorb_tab_host[dd] = make_float2((float)(1.0 / (1.0 + eta)), (float)(eta / (1.0 + eta)));
+        }
+        e = cudaMemcpyAsync(p->absorb_tab, p->absorb_tab_host.data(), sizeof(float2) * tab_n,
+                            cudaMemcpyHostToDevice, p->stream);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "absorbing layer table"));
+        p->device_bytes += (int64_t)(save_bytes + sizeof(float2) * tab_n);
     }
 
     cudaStream_t s = p->stream;

@@ -1,6 +1,7 @@
 // The plan object behind stencil_plan_t, shared by the runtime translation units.
 #pragma once
 
+#include <vector>
 #include <cmath>
 #include <string>
 
@@ -93,6 +94,8 @@ struct Plan {
     float absorb_eta = 0.0f;
     int64_t absorb_shell = 0;
     float *absorb_save = nullptr;
+    float2 *absorb_tab = nullptr;         // device (g_d, h_d), d = 0..W, after the saved values
+    std::vector<float2> absorb_tab_host;
     // failure-path testing (stencil_debug_wait_fault)
     uint32_t fault_tx = 0, wait_ns = 0;
     const float *inj = nullptr;
@@ -117,6 +120,8 @@ struct Plan {
     cudaError_t launch_one(int parity, int step_off, cudaStream_t s) const;
     StepOps step_ops(int step_off) const;
     bool has_step_ops() const;
+    // the absorbing layer runs inside the sweep (tiled kernel, FP32 storage)
+    bool absorb_folded() const;
     int enqueue_eager(int nsteps);
     int enqueue(int nsteps);
     int capture_graphs();

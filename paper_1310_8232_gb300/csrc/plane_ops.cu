@@ -6,7 +6,9 @@
 //                 = (plain update + eta u^{n-1}) / (1+eta),
 //     as a save of u^{n-1} on the layer's points before the sweep overwrites
 //     it and an apply pass after it (eta = eta_max ((W-d)/W)^2 at distance
-//     d < W from the nearest face);
+//     d < W from the nearest face, applied as plain * g_d + u^{n-1} * h_d
+//     with g_d = 1/(1+eta), h_d = eta/(1+eta) from the plan's table; the
+//     tiled FP32 sweep folds the same operations into its own update);
 //   - the point source, when a layer is present (it is added after the
 //     damping, as in the time loop's order);
 //   - the injection of data on a plane (the adjoint source of RTM);
@@ -67,9 +69,8 @@ __device__ __forceinline__ void shell_point_op(const StepOps &o, float *field, i
         o.save[t] = *q;
     } else {
         const int d = min(min(min(x, o.nx - 1 - x), min(y, o.ny - 1 - y)), min(z, o.nz - 1 - z));
-        const float a = (float)(o.absorb_w - d) / (float)o.absorb_w;
-        const float eta = o.absorb_eta * a * a;
-        *q = fmaf(eta, o.save[t], *q) / (1.0f + eta);
+        const float2 g = o.absorb_tab[min(d, o.absorb_w)];
+        *q = fmaf(g.y, o.save[t], *q * g.x);
     }
 }
 

@@ -180,12 +180,14 @@ __device__ __forceinline__ float4 scale4(const float4 &v, float s)
 // One block's work: tile (bx, by) of the xy plane, output planes [z0, z1)
 // of one shot, at time level n.  map_* are the shot's tensor maps (kernel
 // parameters or 64-byte aligned global memory).
-template <int R, int TX, int TY, typename E, bool REC>
+template <int R, int TX, int TY, typename E, bool REC, bool ABS = false>
 __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUtensorMap *map_up,
                                            const CUtensorMap *map_k, const SweepParams &params, int bx, int by,
                                            int z0, int z1, int64_t n_level, unsigned char *smem)
 {
     using S = TiledShape<R, TX, TY, E>;
+    static_assert(!ABS || (S::F32 && !REC), "the folded absorbing layer is an FP32 variant without the energy");
+    constexpr bool SPLIT = S::SPLIT;
     // a private copy: the inline-asm waits and copies clobber memory, which
     // would otherwise force every field to be reloaded after each of them
     const SweepParams p = params;
@@ -299,7 +301,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     const float2 c0x3 = make_float2(3.0f * wf<R>(0), 3.0f * wf<R>(0));
     int done = 0;                           // planes fully processed (block-uniform)
 
-    if constexpr (!S::SPLIT) {
+    if constexpr (!SPLIT) {
         int su_stage = 0, su_phase = 0;     // stage / parity of plane i
         int sa_stage = 0, sa_phase = 0;     // aux stage / parity of output ja = i - 2R
         for (int i0 = 0; i0 < nin; i0 += S::RING) {
@@ -439,6 +441,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float2 oB =
                             __ffma2_rn(hi2(kap[h]), fB, __ffma2_rn(neg1, hi2(prev[h]), __fmul2_rn(two, hi2(cc))));
                         float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
+                        if constexpr (ABS)
+                            absorb4(p.absorb_w, p.absorb_tab, p.nx, p.ny, p.nz, gx, gy0 + h, o, nxt, prev[h]);
                         if (src_here && src_row == h && o == p.src.z) {
                             const int k = p.src.x - gx;
                             if (k == 0) nxt.x += src_add;
@@ -643,6 +647,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float2 oB =
                             __ffma2_rn(hi2(kap), fB, __ffma2_rn(neg1, hi2(prev), __fmul2_rn(two, hi2(cc))));
                         float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
+                        if constexpr (ABS)
+                            absorb4(p.absorb_w, p.absorb_tab, p.nx, p.ny, p.nz, gx, gy0 + h, o, nxt, prev);
                         if (src_plane && src_row == h) {
                             const int q = p.src.x - gx;
                             if (q == 0) nxt.x += src_add;
@@ -748,8 +754,9 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
 }
 
 // One shot per launch: block (tile, z-chunk) from the grid position.  REC:
-// the variant that also sums the step's energy.
-template <int R, int TX, int TY, typename E, bool REC = false>
+// the variant that also sums the step's energy; ABS: the variant with the
+// absorbing layer folded in (FP32).
+template <int R, int TX, int TY, typename E, bool REC = false, bool ABS = false>
 __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
     sweep_tiled_kernel(const __grid_constant__ CUtensorMap map_u, const __grid_constant__ CUtensorMap map_up,
                        const __grid_constant__ CUtensorMap map_k, const SweepParams p)
@@ -760,7 +767,7 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
     const int z0 = blockIdx.y * p.zchunk;
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int64_t n = current_step(p);
-    sweep_tile<R, TX, TY, E, REC>(&map_u, &map_up, &map_k, p, bx, by, z0, z1, n, smem);
+    sweep_tile<R, TX, TY, E, REC, ABS>(&map_u, &map_up, &map_k, p, bx, by, z0, z1, n, smem);
     if (REC && p.energy_on) {
         // block partial (warps in order), then the last block to finish adds
         // all partials in block order: the step's energy, deterministic

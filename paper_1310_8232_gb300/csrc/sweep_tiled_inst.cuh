@@ -30,6 +30,10 @@ struct Inst {
                 if (status == cudaSuccess)
                     status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E, true>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+                if constexpr (S::F32)
+                    if (status == cudaSuccess)
+                        status = cudaFuncSetAttribute(sweep_tiled_kernel<R, TX, TY, E, false, true>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
                 if (status == cudaSuccess)
                     status = cudaFuncSetAttribute(sweep_grouped_kernel<R, TX, TY, E>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -78,7 +82,13 @@ struct Inst {
             q.tiles_x = tiles_x;
             q.zchunk = zc;
             dim3 grid(tiles_x * tiles_y, nzc);
-            if (q.energy_on)
+            if (q.absorb_w > 0) {
+                if constexpr (S::F32)
+                    sweep_tiled_kernel<R, TX, TY, E, false, true>
+                        <<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
+                else
+                    return cudaErrorInvalidValue;            // the layer needs FP32 storage
+            } else if (q.energy_on)
                 sweep_tiled_kernel<R, TX, TY, E, true><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
             else
                 sweep_tiled_kernel<R, TX, TY, E, false><<<grid, S::NT, S::SMEM, s>>>(m.u_halo, m.up_core, m.k_core, q);
