@@ -384,7 +384,7 @@ typedef struct {
     double  hbm_budget_frac;    /* share of the device's total memory the server may hold (default 0.8) */
     int64_t hbm_budget_bytes;   /* > 0: a byte budget instead of the fraction */
     int32_t max_slots;          /* resident shots at most (default 64) */
-    int32_t chunk_steps;        /* time steps per engine iteration (default 20) */
+    int32_t chunk_steps;        /* time steps per lane chunk (default 20) */
     int32_t radius;             /* every shot's radius (default 5) */
     int32_t storage;            /* every shot's storage (default FP32) */
     void   *cuda_stream;        /* NULL = the server creates its lanes' streams; else one lane on it */
@@ -405,9 +405,9 @@ typedef struct {
 typedef struct {
     int64_t submitted, admitted, done, failed, queued, running;
     int64_t bytes_in_use, budget_bytes;
-    int64_t iterations;                 /* engine iterations run */
+    int64_t iterations;                 /* lane chunks run (all lanes) */
     int64_t point_updates;              /* nx*ny*nz*steps summed over finished shots */
-    double  busy_s;                     /* engine time spent stepping resident shots */
+    double  busy_s;                     /* wall time with at least one lane's chunk on the GPU */
     double  admit_s;                    /* engine time spent admitting shots (plan set-up) */
     double  build_s;                    /* engine time spent re-describing the resident set */
     double  retire_s;                   /* retire-thread time (read-back and free) */
