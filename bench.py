@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--record", choices=["none", "energy", "traces", "both"], default="none",
                     help="single: also record the per-step energy and/or a receiver plane at z = 10")
     ap.add_argument("--absorb", type=int, default=0,
-                    help="single: absorbing layer of this many points on every face (eta_max 0.2)")
+                    help="single / batch: absorbing layer of this many points on every face (eta_max 0.2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-timesteps", type=int, default=10)
@@ -246,7 +246,8 @@ def run_batch(args, torch, st, workloads, ranks):
         v = torch.from_numpy(workloads.layered_velocity(nx, ny, nz, seed=sd)).cuda()
         dt = workloads.time_step(st.stencil_cfl_limit(R), workloads.DX, float(v.max()))
         vels.append(v)
-        descs.append(st.make_desc(v, dt, radius=R, dx=workloads.DX, graph_steps=20, stream=stream.cuda_stream))
+        descs.append(st.make_desc(v, dt, radius=R, dx=workloads.DX, graph_steps=20, stream=stream.cuda_stream,
+                                  absorb=(args.absorb, 0.2 if args.absorb else 0.0)))
     pts = float(sum(nx * ny * nz for nx, ny, nz in all_dims)) * T
     batch = st.stencil_batch_create(descs, graph_steps=20)
     plans = [st.stencil_plan(d) for d in descs]
@@ -298,7 +299,7 @@ def run_batch(args, torch, st, workloads, ranks):
                                f"8-layer random models, R={R}, {T} steps each; one grouped launch per step, "
                                f"20-step CUDA graphs", "shots": len(all_dims), "timesteps": T,
                    "parallelism": f"replicas: contiguous shot shares over {ranks.env.world} GPU(s)",
-                   "point_updates": pts, "zchunk": zc},
+                   "point_updates": pts, "zchunk": zc, "absorb": args.absorb},
         "per_shot_loop": {"value": pts / (l_ms / 1e3) / 1e9, "ms_per_step": l_ms,
                           "what": "the same shots, one plan each, stencil_step(100) in a loop (20-step graphs)"},
         "speedup_vs_loop": l_ms / g_ms,

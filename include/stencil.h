@@ -140,10 +140,11 @@ typedef struct {
                                     user_buffers[stats.current_buffer].  They stay the caller's
                                     and must outlive the plan; the shot server does not take them. */
     int32_t absorb_width;        /* absorbing layer: points from each face (0 = none, the plain
-                                    ghost-zero boundary); FP32 storage and single plans only
-                                    (16-bit storage, batches and the shot server refuse it with
-                                    STENCIL_EUNSUPPORTED); run as a save of u^{n-1} on the layer
-                                    before each sweep and a damping pass after it */
+                                    ghost-zero boundary); FP32 storage only (16-bit storage is
+                                    refused with STENCIL_EUNSUPPORTED).  The tiled kernel applies
+                                    it inside the sweep (single plans, batches, the shot server);
+                                    the naive kernel as a save of u^{n-1} on the layer before
+                                    each sweep and a damping pass after it */
     double  absorb_eta;          /* eta = sigma dt at the face, >= 0: the layer solves the damped
                                     equation u_tt + 2 sigma u_t = v^2 Laplacian(u), centred in time,
                                     u^{n+1} = (2u^n - (1-eta) u^{n-1} + kappa Lambda(u^n)) / (1+eta),

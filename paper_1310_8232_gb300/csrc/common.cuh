@@ -106,6 +106,7 @@ struct SweepParams {
 __device__ __forceinline__ void absorb4(int W, const float2 *tab, int nx, int ny, int nz, int gx, int y, int z,
                                         float4 &v, const float4 &prev)
 {
+    if (W <= 0) return;                       // a shot without a layer in a grouped launch
     const int dyz = min(min(z, nz - 1 - z), min(y, ny - 1 - y));
     if (dyz >= W && gx >= W && gx + 3 <= nx - 1 - W) return;
     float *pv = &v.x;

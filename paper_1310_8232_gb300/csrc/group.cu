@@ -68,6 +68,8 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
     }
     n_shots = (int)plans.size();
     h_shots.assign(n_shots, GroupShot{});
+    absorb = false;
+    for (const Plan *p : plans) absorb = absorb || p->absorb_folded();
     h_items.clear();
     int maxnz = 0;
     for (int i = 0; i < n_shots; ++i) {
@@ -81,7 +83,7 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
         g.core[0] = p->maps_core[0];
         g.core[1] = p->maps_core[1];
         g.kcore = p->map_kcore;
-        g.prm = p->params(0, 0);
+        g.prm = p->params(0, 0);            // with the layer's width and table if it has one
         g.prm.zchunk = zchunk;
         g.prm.energy_on = 0;        // grouped launches run the plain sweep
         g.prm.fault_tx = 0;
@@ -140,7 +142,7 @@ int Group::step(int k)
     cudaError_t e;
     auto enqueue = [&](int steps) -> cudaError_t {
         for (int i = 0; i < steps; ++i) {
-            cudaError_t r = launch_grouped(R, storage, tx, ty, d_shots, d_items, n_items, i, stream);
+            cudaError_t r = launch_grouped(R, storage, tx, ty, d_shots, d_items, n_items, i, absorb, stream);
             if (r != cudaSuccess) return r;
         }
         return launch_group_advance(d_shots, n_shots, steps, stream);
@@ -226,9 +228,6 @@ int stencil_batch_create(const stencil_desc *descs, int32_t n, int32_t graph_ste
         b->own_stream = true;
     }
     const int R = descs[0].radius, storage = descs[0].storage;
-    for (int i = 0; i < n; ++i)
-        if (descs[i].absorb_width > 0 && descs[i].absorb_eta > 0.0)
-            return bail(fail(STENCIL_EUNSUPPORTED, "batches run the plain sweep: no absorbing layer"));
     stencil_tile tile = descs[0].tile;
     if (tile.kernel == STENCIL_KERNEL_AUTO) {
         tile.kernel = STENCIL_KERNEL_TILED;

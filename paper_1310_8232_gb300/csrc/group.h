@@ -10,6 +10,7 @@ namespace stencil {
 
 struct Group {
     int R = 5, storage = 0, tx = 64, ty = 16, zchunk = 32;
+    bool absorb = false;            // some shot has an absorbing layer: the absorbing variant
     cudaStream_t stream = nullptr;
     GroupShot *d_shots = nullptr;
     GroupItem *d_items = nullptr;

@@ -92,15 +92,16 @@ cudaError_t launch_tiled_f16(int R, int tx, int ty, const TiledMaps &m, const Sw
 cudaError_t launch_tiled_bf16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
 
 // grouped launch: one time step of every shot in `shots` (device array),
-// n_items blocks, block b doing items[b]
+// n_items blocks, block b doing items[b]; absorb: the variant with the
+// absorbing layer (FP32; shots without a layer pass through it unchanged)
 cudaError_t launch_grouped(int R, int storage, int tx, int ty, const GroupShot *shots, const GroupItem *items,
-                           int n_items, int step_off, cudaStream_t s);
+                           int n_items, int step_off, bool absorb, cudaStream_t s);
 cudaError_t launch_grouped_f32(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
-                               int step_off, cudaStream_t s);
+                               int step_off, bool absorb, cudaStream_t s);
 cudaError_t launch_grouped_f16(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
-                               int step_off, cudaStream_t s);
+                               int step_off, bool absorb, cudaStream_t s);
 cudaError_t launch_grouped_bf16(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items,
-                                int step_off, cudaStream_t s);
+                                int step_off, bool absorb, cudaStream_t s);
 // n[i] = min(n[i] + k, n_end[i]) for the shots of a group
 cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStream_t s);
 

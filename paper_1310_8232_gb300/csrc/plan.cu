@@ -82,11 +82,11 @@ int tiled_blocks_per_sm(int R, int storage, int tx, int ty)
 }
 
 cudaError_t launch_grouped(int R, int storage, int tx, int ty, const GroupShot *shots, const GroupItem *items,
-                           int n_items, int step_off, cudaStream_t s)
+                           int n_items, int step_off, bool absorb, cudaStream_t s)
 {
-    if (storage == STENCIL_FP32) return launch_grouped_f32(R, tx, ty, shots, items, n_items, step_off, s);
-    if (storage == STENCIL_FP16) return launch_grouped_f16(R, tx, ty, shots, items, n_items, step_off, s);
-    if (storage == STENCIL_BF16) return launch_grouped_bf16(R, tx, ty, shots, items, n_items, step_off, s);
+    if (storage == STENCIL_FP32) return launch_grouped_f32(R, tx, ty, shots, items, n_items, step_off, absorb, s);
+    if (storage == STENCIL_FP16) return launch_grouped_f16(R, tx, ty, shots, items, n_items, step_off, absorb, s);
+    if (storage == STENCIL_BF16) return launch_grouped_bf16(R, tx, ty, shots, items, n_items, step_off, absorb, s);
     return cudaErrorInvalidValue;
 }
 

@@ -601,8 +601,8 @@ int shot_submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float *o
     Server *s = reinterpret_cast<Server *>(h);
     if (d->radius != s->cfg.radius) return fail(STENCIL_EINVAL, "radius differs from the server's");
     if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || !d->velocity) return fail(STENCIL_EINVAL, "bad descriptor");
-    if (d->absorb_width > 0 && d->absorb_eta > 0.0)
-        return fail(STENCIL_EUNSUPPORTED, "the shot server runs the plain sweep: no absorbing layer");
+    if (d->absorb_width > 0 && d->absorb_eta > 0.0 && s->cfg.storage != STENCIL_FP32)
+        return fail(STENCIL_EUNSUPPORTED, "an absorbing layer needs FP32 storage");
     if (d->user_buffers[0] || d->user_buffers[1] || d->user_buffers[2])
         return fail(STENCIL_EINVAL, "the shot server allocates its own buffers (user_buffers must be NULL)");
     auto r = std::make_unique<Request>();

@@ -794,10 +794,11 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
 }
 
 // Many shots per launch (one time step of each): block b does work item
-// items[b] of shot items[b].shot.  A shot whose step counter has reached its
+// items[b] of shot items[b].shot.  ABS: the variant with the absorbing layer
+// (shots of the group without one have absorb_w = 0 and pass unchanged).  A shot whose step counter has reached its
 // last step is left as it is (its blocks return at once), so shots with
 // different step counts share one launch sequence.
-template <int R, int TX, int TY, typename E>
+template <int R, int TX, int TY, typename E, bool ABS = false>
 __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
     sweep_grouped_kernel(const GroupShot *shots, const GroupItem *items, int step_off)
 {
@@ -816,8 +817,8 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
         fence_tensormap(&g.core[par ^ 1]);
         fence_tensormap(&g.kcore);
     }
-    sweep_tile<R, TX, TY, E, false>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n,
-                                    smem);
+    sweep_tile<R, TX, TY, E, false, ABS>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n,
+                                         smem);
 }
 
 }  // namespace stencil

@@ -8,7 +8,7 @@ namespace stencil {
     int tiled_blocks_per_sm_##S(int tx, int ty);                                                      \
     cudaError_t launch_tiled_##S(int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s); \
     cudaError_t launch_grouped_##S(int tx, int ty, const GroupShot *shots, const GroupItem *items, int n_items, \
-                                   int step_off, cudaStream_t s);
+                                   int step_off, bool absorb, cudaStream_t s);
 STENCIL_UNIT_DECL(f32_r4)
 STENCIL_UNIT_DECL(f32_r5)
 STENCIL_UNIT_DECL(f16_r4)
@@ -32,10 +32,10 @@ STENCIL_UNIT_DECL(bf16_r5)
                         : cudaErrorInvalidConfiguration;                                              \
     }                                                                                                 \
     cudaError_t launch_grouped_##S(int R, int tx, int ty, const GroupShot *shots, const GroupItem *items, \
-                                   int n_items, int step_off, cudaStream_t s)                        \
+                                   int n_items, int step_off, bool absorb, cudaStream_t s)           \
     {                                                                                                 \
-        return R == 4   ? launch_grouped_##S##_r4(tx, ty, shots, items, n_items, step_off, s)          \
-               : R == 5 ? launch_grouped_##S##_r5(tx, ty, shots, items, n_items, step_off, s)          \
+        return R == 4   ? launch_grouped_##S##_r4(tx, ty, shots, items, n_items, step_off, absorb, s)  \
+               : R == 5 ? launch_grouped_##S##_r5(tx, ty, shots, items, n_items, step_off, absorb, s)  \
                         : cudaErrorInvalidConfiguration;                                              \
     }
 STENCIL_UNIT_DISPATCH(f32)

@@ -37,6 +37,10 @@ struct Inst {
                 if (status == cudaSuccess)
                     status = cudaFuncSetAttribute(sweep_grouped_kernel<R, TX, TY, E>,
                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+                if constexpr (S::F32)
+                    if (status == cudaSuccess)
+                        status = cudaFuncSetAttribute(sweep_grouped_kernel<R, TX, TY, E, true>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
             });
             return status;
         }
@@ -97,7 +101,7 @@ struct Inst {
     }
 
     static cudaError_t launch_grouped(const GroupShot *shots, const GroupItem *items, int n_items, int step_off,
-                                      cudaStream_t s)
+                                      bool absorb, cudaStream_t s)
     {
         if constexpr (!fits) {
             return cudaErrorInvalidConfiguration;
@@ -105,7 +109,14 @@ struct Inst {
             cudaError_t e = prepare();
             if (e != cudaSuccess) return e;
             if (n_items <= 0) return cudaSuccess;
-            sweep_grouped_kernel<R, TX, TY, E><<<n_items, S::NT, S::SMEM, s>>>(shots, items, step_off);
+            if (absorb) {
+                if constexpr (S::F32)
+                    sweep_grouped_kernel<R, TX, TY, E, true><<<n_items, S::NT, S::SMEM, s>>>(shots, items, step_off);
+                else
+                    return cudaErrorInvalidValue;            // the layer needs FP32 storage
+            } else {
+                sweep_grouped_kernel<R, TX, TY, E><<<n_items, S::NT, S::SMEM, s>>>(shots, items, step_off);
+            }
             return cudaGetLastError();
         }
     }

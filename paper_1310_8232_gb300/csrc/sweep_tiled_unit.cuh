@@ -38,9 +38,9 @@ cudaError_t UNIT_CAT(launch_tiled, UNIT_NAME)(int tx, int ty, const TiledMaps &m
     return cudaErrorInvalidConfiguration;
 }
 cudaError_t UNIT_CAT(launch_grouped, UNIT_NAME)(int tx, int ty, const GroupShot *shots, const GroupItem *items,
-                                                int n_items, int step_off, cudaStream_t s)
+                                                int n_items, int step_off, bool absorb, cudaStream_t s)
 {
-    UNIT_TILES(UNIT_R, UNIT_E, return I::launch_grouped(shots, items, n_items, step_off, s))
+    UNIT_TILES(UNIT_R, UNIT_E, return I::launch_grouped(shots, items, n_items, step_off, absorb, s))
     return cudaErrorInvalidConfiguration;
 }
 

@@ -40,11 +40,11 @@ def shot(i, shape, R=5, storage=0):
     return v, dt, src
 
 
-def alone(env, v, dt, src, steps, R=5, storage=0):
+def alone(env, v, dt, src, steps, R=5, storage=0, absorb=(0, 0.0)):
     torch, st = env
     # the tiled kernel, as batches and the server run it
     plan = st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, storage=storage, tile=(2, 64, 16, -1),
-                                        stream=stream(torch)))
+                                        absorb=absorb, stream=stream(torch)))
     try:
         out = np.empty_like(v)
         st.stencil_run(plan, steps, out)
@@ -245,3 +245,43 @@ def test_server_on_callers_stream_and_bad_lane_count(env):
     finally:
         st.shot_server_destroy(server)
     assert np.array_equal(out, alone(env, v, dt, src, 10))
+
+
+def test_batch_and_server_with_absorbing_layers_equal_alone(env):
+    """Shots with and without an absorbing layer in one batch (the grouped
+    absorbing variant) and through the shot server: bit-identical to each
+    shot alone, and the layer matches the FP64 oracle."""
+    torch, st = env
+    layers = [(6, 0.25), (0, 0.0), (9, 0.15), (4, 0.3)]
+    shapes = [(67, 45, 33), (96, 64, 40), (40, 40, 40), (130, 20, 51)]
+    shots = [shot(40 + i, s) for i, s in enumerate(shapes)]
+    descs = [st.make_desc(v, dt, radius=5, src=src, absorb=a, stream=stream(torch))
+             for (v, dt, src), a in zip(shots, layers)]
+    b = st.stencil_batch_create(descs)
+    try:
+        st.stencil_batch_run(b, 37)
+        st.stencil_batch_sync(b)
+        outs = []
+        for i, (v, dt, src) in enumerate(shots):
+            out = np.empty_like(v)
+            st.stencil_get_field(st.stencil_batch_plan(b, i), 0, out)
+            outs.append(out)
+    finally:
+        st.stencil_batch_destroy(b)
+    for (v, dt, src), a, out in zip(shots, layers, outs):
+        assert np.array_equal(out, alone(env, v, dt, src, 37, absorb=a))
+    v, dt, src = shots[0]
+    ref, _, _ = oracle.run_ext(v, workloads.DX, dt, 5, 37, src=src, absorb=layers[0])
+    assert oracle.rel_l2(outs[0], ref) <= 1e-5
+    server = make_server(st, chunk_steps=5)
+    jobs = []
+    try:
+        for (v, dt, src), a in zip(shots, layers):
+            out = np.full_like(v, np.nan)
+            jobs.append((st.shot_submit(server, st.make_desc(v, dt, radius=5, src=src, absorb=a), 23, out), out))
+        for t, _ in jobs:
+            assert st.shot_wait(server, t, 60.0) == st.SHOT_DONE
+    finally:
+        st.shot_server_destroy(server)
+    for ((v, dt, src), a), (t, out) in zip(zip(shots, layers), jobs):
+        assert np.array_equal(out, alone(env, v, dt, src, 23, absorb=a))

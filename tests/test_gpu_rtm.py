@@ -165,7 +165,7 @@ def test_unsupported_combinations_are_refused(env):
         assert ei.value.code == st.STENCIL_EUNSUPPORTED
     finally:
         st.stencil_destroy(plan)
-    d = st.make_desc(v, dt, radius=4, absorb=(4, 0.2), stream=s)
-    with pytest.raises(st.StencilError) as ei:             # batches run the plain sweep
+    d = st.make_desc(v, dt, radius=4, absorb=(4, 0.2), storage=1, stream=s)
+    with pytest.raises(st.StencilError) as ei:             # nor in a 16-bit batch
         st.stencil_batch_create([d])
     assert ei.value.code == st.STENCIL_EUNSUPPORTED
