@@ -3,9 +3,11 @@
  * no CUDA headers, no torch) and that every call behaves from C.
  *
  *   abi_client host            host-side calls only (no GPU needed)
+ *   abi_client layout          size and field offsets of every struct of the header
  *   abi_client run OUT.bin     one 40 x 36 x 30 shot, R = 5, 12 steps, written to OUT.bin
  */
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -115,8 +117,117 @@ static int run(const char *path)
     return 0;
 }
 
+/* as the C compiler lays the header's structs out, for the Python
+ * binding's ctypes mirrors to be compared against */
+#define SZ(T) printf(#T " %zu\n", sizeof(T))
+#define OF(T, f) printf(#T "." #f " %zu\n", offsetof(T, f))
+static void layout(void)
+{
+    SZ(stencil_tile);
+    OF(stencil_tile, kernel);
+    OF(stencil_tile, tx);
+    OF(stencil_tile, ty);
+    OF(stencil_tile, zchunk);
+    SZ(stencil_tune_params);
+    OF(stencil_tune_params, parts);
+    OF(stencil_tune_params, iterations);
+    OF(stencil_tune_params, streams);
+    OF(stencil_tune_params, groups);
+    SZ(stencil_desc);
+    OF(stencil_desc, nx);
+    OF(stencil_desc, ny);
+    OF(stencil_desc, nz);
+    OF(stencil_desc, radius);
+    OF(stencil_desc, dx);
+    OF(stencil_desc, dt);
+    OF(stencil_desc, velocity);
+    OF(stencil_desc, velocity_on_device);
+    OF(stencil_desc, src_x);
+    OF(stencil_desc, src_y);
+    OF(stencil_desc, src_z);
+    OF(stencil_desc, src_freq_hz);
+    OF(stencil_desc, src_t0);
+    OF(stencil_desc, src_amp);
+    OF(stencil_desc, storage);
+    OF(stencil_desc, tune_mode);
+    OF(stencil_desc, tile);
+    OF(stencil_desc, tune);
+    OF(stencil_desc, cuda_stream);
+    OF(stencil_desc, graph_steps);
+    OF(stencil_desc, user_buffers);
+    OF(stencil_desc, absorb_width);
+    OF(stencil_desc, absorb_eta);
+    SZ(stencil_stats);
+    OF(stencil_stats, steps_done);
+    OF(stencil_stats, tile);
+    OF(stencil_stats, vmax);
+    OF(stencil_stats, cfl);
+    OF(stencil_stats, cfl_limit);
+    OF(stencil_stats, pitch);
+    OF(stencil_stats, field_bytes);
+    OF(stencil_stats, device_bytes);
+    OF(stencil_stats, min_time_ms);
+    OF(stencil_stats, actual_time_ms);
+    OF(stencil_stats, full_time_ms);
+    OF(stencil_stats, quality);
+    OF(stencil_stats, selection_ms);
+    OF(stencil_stats, n_candidates);
+    OF(stencil_stats, tune_mode);
+    OF(stencil_stats, current_buffer);
+    OF(stencil_stats, user_buffers);
+    SZ(stencil_record_cfg);
+    OF(stencil_record_cfg, receiver_z);
+    OF(stencil_record_cfg, receiver_y);
+    OF(stencil_record_cfg, energy);
+    OF(stencil_record_cfg, capacity);
+    SZ(stencil_inject_cfg);
+    OF(stencil_inject_cfg, z);
+    OF(stencil_inject_cfg, y);
+    OF(stencil_inject_cfg, data);
+    OF(stencil_inject_cfg, steps);
+    OF(stencil_inject_cfg, reverse);
+    OF(stencil_inject_cfg, scale);
+    SZ(shot_server_cfg);
+    OF(shot_server_cfg, hbm_budget_frac);
+    OF(shot_server_cfg, hbm_budget_bytes);
+    OF(shot_server_cfg, max_slots);
+    OF(shot_server_cfg, chunk_steps);
+    OF(shot_server_cfg, radius);
+    OF(shot_server_cfg, storage);
+    OF(shot_server_cfg, cuda_stream);
+    OF(shot_server_cfg, tile);
+    OF(shot_server_cfg, lanes);
+    OF(shot_server_cfg, pad);
+    SZ(shot_timing);
+    OF(shot_timing, t_submit);
+    OF(shot_timing, t_admit);
+    OF(shot_timing, t_done);
+    OF(shot_timing, steps_done);
+    OF(shot_timing, status);
+    OF(shot_timing, pad);
+    SZ(shot_server_stats);
+    OF(shot_server_stats, submitted);
+    OF(shot_server_stats, admitted);
+    OF(shot_server_stats, done);
+    OF(shot_server_stats, failed);
+    OF(shot_server_stats, queued);
+    OF(shot_server_stats, running);
+    OF(shot_server_stats, bytes_in_use);
+    OF(shot_server_stats, budget_bytes);
+    OF(shot_server_stats, iterations);
+    OF(shot_server_stats, point_updates);
+    OF(shot_server_stats, busy_s);
+    OF(shot_server_stats, admit_s);
+    OF(shot_server_stats, build_s);
+    OF(shot_server_stats, retire_s);
+}
+
 int main(int argc, char **argv)
 {
+    if (argc >= 2 && strcmp(argv[1], "layout") == 0) {
+        layout();
+        return 0;
+    }
     if (argc >= 2 && strcmp(argv[1], "host") == 0) {
         host_checks();
         if (fails) return 1;
@@ -124,6 +235,6 @@ int main(int argc, char **argv)
         return 0;
     }
     if (argc >= 3 && strcmp(argv[1], "run") == 0) return run(argv[2]);
-    fprintf(stderr, "usage: abi_client host | run OUT.bin\n");
+    fprintf(stderr, "usage: abi_client host | layout | run OUT.bin\n");
     return 2;
 }

@@ -31,6 +31,25 @@ def test_c_client_host_calls(client):
     assert "host ok" in r.stdout
 
 
+def test_binding_structs_match_the_c_layout(client):
+    """Every ctypes mirror in the binding has the size and field offsets the
+    C compiler gives the header's struct (an added, dropped or reordered
+    field on either side fails here)."""
+    import ctypes
+    from paper_1310_8232_gb300 import binding as st
+    r = subprocess.run([client, "layout"], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    c = dict(line.rsplit(" ", 1) for line in r.stdout.strip().splitlines())
+    seen = 0
+    for key, value in c.items():
+        name, _, field = key.partition(".")
+        cls = getattr(st, name)
+        got = ctypes.sizeof(cls) if not field else getattr(cls, field).offset
+        assert got == int(value), (key, got, value)
+        seen += 1
+    assert seen > 90
+
+
 @pytest.mark.gpu
 def test_c_client_shot_equals_python_binding(client, tmp_path):
     torch = pytest.importorskip("torch")
