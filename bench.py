@@ -36,8 +36,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GPt-updates/s"
 BYTES_PER_POINT = 16            # algorithmic minimum, FP32: u, u_prev, kappa read; u_next written
-# the storage's own minimum: 16-bit u, u_prev, u_next and FP32 kappa
-OWN_BYTES = {"fp32": 16, "fp16": 10, "bf16": 10}
+# the storage's own minimum: 16-bit storage reads u^n, d^n (2 B each) and
+# kappa (4 B) and writes u^{n+1}, d^{n+1} (2 B each)
+OWN_BYTES = {"fp32": 16, "fp16": 12, "bf16": 12}
 STORAGE_ID = {"fp32": 0, "fp16": 1, "bf16": 2}
 FALLBACK_HBM_GBS = 6800.0
 
@@ -203,7 +204,7 @@ def run_reference(args):
     from paper_1310_8232_gb300 import workloads
     v = workloads.layered_velocity(args.n, args.n, args.n, seed=1310).astype(np.float64)
     dt = workloads.time_step(oracle.cfl_limit(args.radius), workloads.DX, float(v.max()))
-    per = max(1, min(args.cpu_timesteps, 2))
+    per = max(1, args.cpu_timesteps)
     for _ in range(args.warmup):
         oracle.run(v, workloads.DX, dt, args.radius, per)
     times = []

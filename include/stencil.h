@@ -382,7 +382,8 @@ STENCIL_API int stencil_batch_destroy(stencil_batch_t b);
 typedef struct shot_server_s *shot_server_t;
 
 typedef struct {
-    double  hbm_budget_frac;    /* share of the device's total memory the server may hold (default 0.8) */
+    double  hbm_budget_frac;    /* share of the device memory free at shot_server_create that the server
+                                   may hold (default 0.8) */
     int64_t hbm_budget_bytes;   /* > 0: a byte budget instead of the fraction */
     int32_t max_slots;          /* resident shots at most (default 64) */
     int32_t chunk_steps;        /* time steps per lane chunk (default 20) */

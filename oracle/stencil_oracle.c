@@ -238,6 +238,8 @@ int oracle_run(const oracle_problem *p, int steps, int bi, int bj, int bk,
     double *const u_out = u, *const up_out = u_prev;
     double *next = spare;
     const double dt2 = p->dt * p->dt, dx2 = p->dx * p->dx;
+    /* each element's expression is independent of the thread count */
+    #pragma omp parallel for schedule(static)
     for (long q = 0; q < n; ++q) kappa[q] = p->v[q] * p->v[q] * dt2 / dx2;
     const int has_src = p->amp != 0.0 && p->sx >= 0 && p->sx < nx && p->sy >= 0 &&
                         p->sy < ny && p->sz >= 0 && p->sz < nz;

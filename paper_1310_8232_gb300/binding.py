@@ -405,12 +405,29 @@ def stencil_select_ob(times) -> tuple[int, int, float]:
 
 def stencil_sqdiff_noalloc(a, a_pitch: int, b, nx: int, ny: int, nz: int, out, stream=None) -> None:
     """out[0] = sum (a-b)^2, out[1] = sum b^2 (FP64, device), with no device allocation.
-    a: FP32 CUDA tensor (row pitch a_pitch), b: FP64 CUDA tensor, out: 2-element FP64 CUDA tensor."""
+    a: FP32 CUDA tensor (row pitch a_pitch), b: FP64 CUDA tensor, out: 2-element FP64 CUDA tensor.
+
+    The C entry point receives bare pointers and cannot see how large the
+    buffers are, so the types and sizes are checked here: a holds at least
+    (ny*nz - 1) * a_pitch + nx FP32 values, b at least nx*ny*nz FP64 values,
+    out at least 2 FP64 values, all contiguous."""
     pa, da = _ptr(a)
     pb, db = _ptr(b)
     po, do = _ptr(out)
     if not (da and db and do):
         raise ValueError("a, b and out must be CUDA tensors")
+    import torch
+    if nx <= 0 or ny <= 0 or nz <= 0 or a_pitch < nx:
+        raise ValueError("need nx, ny, nz > 0 and a_pitch >= nx")
+    rows = ny * nz
+    for name, t, dtype, need in (("a", a, torch.float32, (rows - 1) * a_pitch + nx),
+                                 ("b", b, torch.float64, nx * rows), ("out", out, torch.float64, 2)):
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < need:
+            raise ValueError(f"{name} holds {t.numel()} values, the sizes need {need}")
     _check(_lib.stencil_sqdiff_noalloc(pa, a_pitch, pb, nx, ny, nz, po, int(stream) if stream else None))
 
 

@@ -2,17 +2,18 @@
 //
 // The state that determines every later step of the leapfrog recursion
 // (Sec. 2, Algorithm 1's time loop) is the pair of levels (u^n, u^{n-1}) and
-// n itself (the source term reads w(n dt)).  16-bit storage adds the
-// per-plane scales of those two levels and their per-plane maxima, from which
-// the scale of level n+1 is derived.  A checkpoint holds exactly that, in
-// the storage's own encoding, so a restored plan continues bit for bit.
+// n itself (the source term reads w(n dt)).  16-bit storage keeps u^n and
+// the difference d^n = u^n - u^{n-1} instead, plus the per-plane scales of
+// both and their per-plane maxima, from which the scales of level n+1 are
+// derived.  A checkpoint holds exactly that, in the storage's own encoding,
+// so a restored plan continues bit for bit.
 //
 // Layout (little-endian, as the host writes it):
 //   CkptHeader (128 bytes)
-//   u^n      nx*ny*nz elements of esize bytes, dense (x fastest)
-//   u^{n-1}  same
-//   16-bit storage only: scale[n], scale[n-1] (nz floats each),
-//                        amax[n],  amax[n-1]  (nz uint32 each)
+//   u^n              nx*ny*nz elements of esize bytes, dense (x fastest)
+//   u^{n-1} (FP32)   same; d^n for 16-bit storage
+//   16-bit storage only: scale of u^n, scale of d^n (nz floats each),
+//                        amax of u^n,  amax of d^n  (nz uint32 each)
 #include <cstring>
 
 #include "plan_impl.h"
@@ -21,7 +22,7 @@ namespace stencil {
 namespace {
 
 constexpr char MAGIC[8] = {'S', 'T', 'N', 'C', 'K', 'P', 'T', '1'};
-constexpr uint32_t VERSION = 1;
+constexpr uint32_t VERSION = 2;   // 2: 16-bit storage holds (u^n, d^n)
 
 struct CkptHeader {
     char magic[8];
@@ -82,18 +83,18 @@ struct Piece {
 
 int pieces(Plan *p, Piece out[6], int *n)
 {
-    const int64_t level = p->steps_done;
+    const int64_t at = (int64_t)slot_of(p->steps_done) * p->nz;
     int k = 0;
+    // u^n, then u^{n-1} (FP32) or d^n (16-bit)
     for (int w = 0; w < 2; ++w)
-        out[k++] = {static_cast<char *>(p->buf[p->cur ^ w]), (size_t)p->pitch * p->esize, (size_t)p->nx * p->esize,
-                    (size_t)p->ny * p->nz};
+        out[k++] = {w == 0 ? p->bptr(p->cur, 0) : p->aux_ptr(p->cur, 0), (size_t)p->pitch * p->esize,
+                    (size_t)p->nx * p->esize, (size_t)p->ny * p->nz};
     if (p->storage != STENCIL_FP32) {
-        for (int w = 0; w < 2; ++w)
-            out[k++] = {reinterpret_cast<char *>(p->d_scale + (int64_t)slot_of(level - w) * p->nz),
-                        sizeof(float) * p->nz, sizeof(float) * p->nz, 1};
-        for (int w = 0; w < 2; ++w)
-            out[k++] = {reinterpret_cast<char *>(p->d_amax + (int64_t)slot_of(level - w) * p->nz),
-                        sizeof(unsigned) * p->nz, sizeof(unsigned) * p->nz, 1};
+        const size_t sb = sizeof(float) * p->nz, ab = sizeof(unsigned) * p->nz;
+        out[k++] = {reinterpret_cast<char *>(p->d_scale + at), sb, sb, 1};
+        out[k++] = {reinterpret_cast<char *>(p->d_scale_d + at), sb, sb, 1};
+        out[k++] = {reinterpret_cast<char *>(p->d_amax + at), ab, ab, 1};
+        out[k++] = {reinterpret_cast<char *>(p->d_amax_d + at), ab, ab, 1};
     }
     *n = k;
     return STENCIL_OK;
@@ -187,8 +188,12 @@ int stencil_restore(stencil_plan_t h, const void *src, uint64_t bytes, int32_t o
     }
     if (e == cudaSuccess && p->d_amax) {
         // the maxima of the next two levels are accumulated from zero
-        for (int64_t level = hd.step + 1; level <= hd.step + 2 && e == cudaSuccess; ++level)
+        for (int64_t level = hd.step + 1; level <= hd.step + 2 && e == cudaSuccess; ++level) {
             e = cudaMemsetAsync(p->d_amax + (int64_t)slot_of(level) * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(p->d_amax_d + (int64_t)slot_of(level) * p->nz, 0, sizeof(unsigned) * p->nz,
+                                    p->stream);
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(p->d_step, &hd.step, sizeof hd.step, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "restore copy");

@@ -66,13 +66,19 @@ struct SweepParams {
     int64_t pitch;                 // row pitch, elements (same for the wavefields and kappa)
     int64_t plane;                 // pitch * ny
     const void *u;                 // u^n (FP32, or FP16/BF16 scaled per plane)
-    void *up;                      // in: u^{n-1}; out: u^{n+1} (in place)
+    void *up;                      // FP32: in u^{n-1}, out u^{n+1} (in place); 16-bit: out u^{n+1}
     const float *kappa;            // v^2 dt^2 / dx^2
-    // reduced-precision storage only: per-plane power-of-two scales and
-    // amax (float bit patterns) of the time levels, slot = level mod 4
+    // reduced-precision storage only.  The state is (u^n, d^n) with the
+    // difference d^n = u^n - u^{n-1} stored instead of u^{n-1}; d is updated
+    // in place (in d^n, out d^{n+1}).  Per-plane power-of-two scales and
+    // amax (float bit patterns) of each time level, slot = level mod 4, for
+    // u (scale, amax) and for d (scale_d, amax_d).
+    void *dv;                      // [field] d^n -> d^{n+1}
     float *scale;                  // [4][nz]
     unsigned *amax;                // [4][nz]
-    float growth;                  // 2 + kappa_max * 3W: bound on |u^{n+1}| / max |u^n| near a point
+    float *scale_d;                // [4][nz]
+    unsigned *amax_d;              // [4][nz]
+    float growth;                  // kappa_max * 3W: bound on |kappa Lambda(u)| / max |u| over the star
     float src_bound;               // |source amplitude|, |w| <= 1
     int32_t zchunk;                // planes per thread block in z
     int32_t tiles_x;               // tiles along x (tiled kernel)
@@ -124,7 +130,7 @@ __device__ __forceinline__ void absorb4(int W, const float2 *tab, int nx, int ny
 // buffers and parameters, in 64-byte aligned device memory.
 struct alignas(64) GroupShot {
     CUtensorMap halo[2];           // u^n halo boxes, by which buffer holds u^n
-    CUtensorMap core[2];           // u^{n-1} core boxes, by buffer
+    CUtensorMap core[2];           // FP32: u^{n-1} core boxes, by buffer; 16-bit: the d box (both)
     CUtensorMap kcore;             // kappa
     SweepParams prm;               // u, up are set per step from buf[]
     void *buf[2];

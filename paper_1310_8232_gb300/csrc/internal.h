@@ -106,12 +106,16 @@ cudaError_t launch_grouped_bf16(int R, int tx, int ty, const GroupShot *shots, c
 cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStream_t s);
 
 // ---- K2 helpers: 16-bit fields <-> FP32 with per-plane power-of-two scales ----
-// pack: src FP32 (pitch elements) -> dst 16-bit; writes amax[z] (max |src|
-// over plane z, float bits) and scale[z] (the power of two used).
-cudaError_t launch_pack16(int storage, const float *src, void *dst, int nx, int ny, int nz, int64_t pitch,
-                          float *scale, unsigned *amax, cudaStream_t s);
+// pack: v = src (or src - sub when sub is not null), FP32 (pitch elements)
+// -> dst 16-bit; writes amax[z] (max |v| over plane z, float bits) and
+// scale[z] (the power of two used).
+cudaError_t launch_pack16(int storage, const float *src, const float *sub, void *dst, int nx, int ny, int nz,
+                          int64_t pitch, float *scale, unsigned *amax, cudaStream_t s);
 // unpack: 16-bit src with scale[z] -> FP32 dst (same pitch)
 cudaError_t launch_unpack16(int storage, const void *src, float *dst, int nx, int ny, int nz, int64_t pitch,
                             const float *scale, cudaStream_t s);
+// u^{n-1} = u^n - d^n in FP32 from the 16-bit u and d and their plane scales
+cudaError_t launch_unpack16_prev(int storage, const void *u, const void *d, float *dst, int nx, int ny, int nz,
+                                 int64_t pitch, const float *scale_u, const float *scale_d, cudaStream_t s);
 
 }  // namespace stencil

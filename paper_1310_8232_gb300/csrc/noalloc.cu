@@ -66,14 +66,24 @@ __global__ void __launch_bounds__(NA_THREADS)
     const int64_t begin = (int64_t)blockIdx.x * NA_PER_BLOCK;
     const int64_t end = min(n, begin + NA_PER_BLOCK);
     double d2 = 0.0, r2 = 0.0;
-    for (int64_t i = begin + threadIdx.x; i < end; i += NA_THREADS) {
-        const int64_t row = i / nx;
-        const int x = (int)(i - row * nx);
+    // (row, x) of this thread's first element by one division; each stride
+    // of NA_THREADS elements then moves it by (dq rows, dr columns)
+    const int64_t i0 = begin + threadIdx.x;
+    int64_t row = i0 / nx;
+    int x = (int)(i0 - row * nx);
+    const int dq = NA_THREADS / nx, dr = NA_THREADS % nx;
+    for (int64_t i = i0; i < end; i += NA_THREADS) {
         const double av = (double)a[row * pitch + x];
         const double bv = b[i];
         const double d = av - bv;
         d2 += d * d;
         r2 += bv * bv;
+        x += dr;
+        row += dq;
+        if (x >= nx) {
+            x -= nx;
+            ++row;
+        }
     }
     (void)ny;
     na_block_sum2(d2, r2, partials + 2 * blockIdx.x);

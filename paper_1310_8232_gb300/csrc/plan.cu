@@ -165,11 +165,13 @@ int Plan::build_maps()
     TiledInfo info;
     if (!tiled_config(R, storage, tile.tx, tile.ty, &info))
         return fail(STENCIL_EUNSUPPORTED, "tile %dx%d not built for radius %d", tile.tx, tile.ty, R);
+    // maps_core[b] is the point-wise operand read when u^n is in buf[b ^ 1]:
+    // u^{n-1} = buf[b] (FP32), or the one d buffer (16-bit)
     for (int b = 0; b < 2; ++b) {
         int rc = encode_map(&maps_halo[b], buf[b], nx, ny, nz, pitch, esize, tile.tx + 2 * info.hx,
                             tile.ty + 2 * R);
         if (rc) return rc;
-        rc = encode_map(&maps_core[b], buf[b], nx, ny, nz, pitch, esize, tile.tx, tile.ty);
+        rc = encode_map(&maps_core[b], aux_ptr(b ^ 1, 0), nx, ny, nz, pitch, esize, tile.tx, tile.ty);
         if (rc) return rc;
     }
     return encode_map(&map_kcore, kappa, nx, ny, nz, pitch, 4, tile.tx, tile.ty);
@@ -185,6 +187,7 @@ SweepParams Plan::params(int parity, int step_off) const
     s.plane = pitch * ny;
     s.u = buf[parity];
     s.up = buf[parity ^ 1];
+    s.dv = dbuf;
     s.kappa = kappa;
     s.zchunk = tile.zchunk > 0 ? tile.zchunk : nz;
     s.tiles_x = 0;
@@ -194,6 +197,8 @@ SweepParams Plan::params(int parity, int step_off) const
     s.err = d_err;
     s.scale = d_scale;
     s.amax = d_amax;
+    s.scale_d = d_scale_d;
+    s.amax_d = d_amax_d;
     s.growth = growth;
     s.src_bound = src_bound;
     s.energy = rec_energy;
@@ -382,6 +387,8 @@ void Plan::release()
             if (b) dev_free(b);
         if (kappa) dev_free(kappa);
     }
+    if (dbuf) dev_free(dbuf);
+    dbuf = nullptr;
     for (auto &b : staging)
         if (b) dev_free(b);
     staging[0] = staging[1] = nullptr;
@@ -426,10 +433,11 @@ int Plan::load_velocity(const float *v, int on_device)
     cfl = (double)vm * dt / dx;
     if (cfl > cfl_lim * (1.0 + 1e-12))
         return fail(STENCIL_ECFL, "vmax*dt/dx = %.6g exceeds the stability bound %.6g", cfl, cfl_lim);
-    // |u^{n+1}| <= (2 + kappa_max * sum |weights|) max|u^n| + |u^{n-1}|; sum
-    // |weights| over the 3D star = 3W with 3W = 4 / cfl_limit^2
+    // |kappa Lambda(u)| <= kappa_max * sum |weights| * max |u| over the star;
+    // sum |weights| over the 3D star = 3W with 3W = 4 / cfl_limit^2 (the
+    // 16-bit storage's scale bound on the step's change of d)
     const double kmax = cfl * cfl;
-    growth = (float)((2.0 + kmax * 4.0 / (cfl_lim * cfl_lim)) * (1.0 + 1e-6));
+    growth = (float)(kmax * 4.0 / (cfl_lim * cfl_lim) * (1.0 + 1e-6));
     velocity_ok = true;
     return STENCIL_OK;
 }
@@ -467,10 +475,13 @@ int Plan::fp32_level(int which, const float **out)
     }
     int rc = ensure_staging();
     if (rc) return rc;
-    const int64_t level = steps_done - which;
-    const int slot = (int)(((level % 4) + 4) % 4);
-    cudaError_t e = launch_unpack16(storage, buf[cur ^ which], staging[which], nx, ny, nz, pitch,
-                                    d_scale + (int64_t)slot * nz, stream);
+    // u^n from buf[cur]; u^{n-1} = u^n - d^n
+    const int slot = (int)(((steps_done % 4) + 4) % 4);
+    cudaError_t e =
+        which == 0
+            ? launch_unpack16(storage, buf[cur], staging[0], nx, ny, nz, pitch, d_scale + (int64_t)slot * nz, stream)
+            : launch_unpack16_prev(storage, buf[cur], dbuf, staging[1], nx, ny, nz, pitch,
+                                   d_scale + (int64_t)slot * nz, d_scale_d + (int64_t)slot * nz, stream);
     if (e != cudaSuccess) return fail_cuda(e, "unpack");
     *out = staging[which];
     return STENCIL_OK;
@@ -661,10 +672,15 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
         e = p->dev_alloc(reinterpret_cast<void **>(&p->kappa), kbytes);
         if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(kappa)"));
     }
+    if (p->storage != STENCIL_FP32) {
+        e = p->dev_alloc(&p->dbuf, fbytes);
+        if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(difference field)"));
+    }
     // scratch: step counter, error word, v range, reduction partials and
-    // result, and (16-bit storage) the per-level per-plane scale and amax tables
+    // result, and (16-bit storage) the per-level per-plane scale and amax
+    // tables of u and d, 4 x [4][nz] x 4 bytes
     const size_t red_bytes = 256 + sizeof(double) * (2 * RED_BLOCKS + 8);
-    const size_t tab_bytes = p->storage == STENCIL_FP32 ? 0 : (size_t)8 * 4 * d->nz;
+    const size_t tab_bytes = p->storage == STENCIL_FP32 ? 0 : (size_t)16 * 4 * d->nz;
     const size_t scratch = red_bytes + tab_bytes;
     e = p->dev_alloc(&p->d_scratch, scratch);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(scratch)"));
@@ -676,10 +692,14 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     p->d_result = reinterpret_cast<double *>(sc + 64);
     p->d_partials = reinterpret_cast<double *>(sc + 256);
     if (tab_bytes) {
+        const size_t tab = 4 * 4 * (size_t)d->nz;
         p->d_scale = reinterpret_cast<float *>(sc + red_bytes);
-        p->d_amax = reinterpret_cast<unsigned *>(sc + red_bytes + 4 * 4 * (size_t)d->nz);
+        p->d_amax = reinterpret_cast<unsigned *>(sc + red_bytes + tab);
+        p->d_scale_d = reinterpret_cast<float *>(sc + red_bytes + 2 * tab);
+        p->d_amax_d = reinterpret_cast<unsigned *>(sc + red_bytes + 3 * tab);
     }
-    p->device_bytes = (p->user_owned ? 0 : 2 * (int64_t)fbytes + (int64_t)kbytes) + (int64_t)scratch;
+    p->device_bytes = (p->user_owned ? 0 : 2 * (int64_t)fbytes + (int64_t)kbytes) + (int64_t)scratch +
+                      (p->dbuf ? (int64_t)fbytes : 0);
     if (p->absorb_w > 0) {
         // u^{n-1} of the layer's points, saved before each sweep
         p->absorb_shell = shell_points(d->nx, d->ny, d->nz, p->absorb_w);
@@ -707,7 +727,8 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
     if ((e = cudaMemsetAsync(p->d_scratch, 0, scratch, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->buf[0], 0, fbytes, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(p->buf[1], 0, fbytes, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->kappa, 0, kbytes, s)) != cudaSuccess)
+        (e = cudaMemsetAsync(p->kappa, 0, kbytes, s)) != cudaSuccess ||
+        (p->dbuf && (e = cudaMemsetAsync(p->dbuf, 0, fbytes, s)) != cudaSuccess))
         return bail(fail_cuda(e, "cudaMemsetAsync"));
     float v_src = 0.0f;
     if (d->src_amp != 0.0) {
@@ -860,36 +881,36 @@ int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, in
         int rc = p->ensure_staging();
         if (rc) return rc;
     }
+    // FP32: straight into the two level buffers.  16-bit: both levels staged
+    // in FP32 (zeros where not given), then u^n and d^n = u^n - u^{n-1}
+    // packed with the scales of level `step`.
     for (int k = 0; k < 2; ++k) {
-        void *dst = p->buf[p->cur ^ k];
-        const int64_t level = step - k;
-        const int slot = (int)(((level % 4) + 4) % 4);
+        float *dst = p->storage == STENCIL_FP32 ? static_cast<float *>(p->buf[p->cur ^ k]) : p->staging[k];
         cudaError_t e;
-        if (!src[k]) {
-            e = cudaMemsetAsync(dst, 0, (size_t)p->field_elems * p->esize, p->stream);
-            if (e == cudaSuccess && p->d_amax)
-                e = cudaMemsetAsync(p->d_amax + (int64_t)slot * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
-            if (e == cudaSuccess && p->d_scale)
-                e = cudaMemsetAsync(p->d_scale + (int64_t)slot * p->nz, 0, sizeof(float) * p->nz, p->stream);
-        } else {
-            float *stage = p->storage == STENCIL_FP32 ? static_cast<float *>(dst) : p->staging[0];
-            e = memcpy_rows(stage, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
-                                  (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
-                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream);
-            if (e == cudaSuccess && p->storage != STENCIL_FP32)
-                e = launch_pack16(p->storage, stage, dst, p->nx, p->ny, p->nz, p->pitch,
-                                  p->d_scale + (int64_t)slot * p->nz, p->d_amax + (int64_t)slot * p->nz, p->stream);
-        }
+        if (!src[k])
+            e = cudaMemsetAsync(dst, 0, (size_t)p->field_elems * sizeof(float), p->stream);
+        else
+            e = memcpy_rows(dst, p->pitch * sizeof(float), src[k], (size_t)p->nx * sizeof(float),
+                            (size_t)p->nx * sizeof(float), (size_t)p->ny * p->nz,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, p->stream);
         if (e != cudaSuccess) return fail_cuda(e, "field copy in");
     }
-    if (p->d_amax) {
-        // the slots the next two steps write must start from zero
-        for (int64_t level = step + 1; level <= step + 2; ++level) {
-            const int slot = (int)(level % 4);
-            cudaError_t e =
-                cudaMemsetAsync(p->d_amax + (int64_t)slot * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
-            if (e != cudaSuccess) return fail_cuda(e, "amax reset");
+    if (p->storage != STENCIL_FP32) {
+        const int64_t slot = step % 4;
+        cudaError_t e = launch_pack16(p->storage, p->staging[0], nullptr, p->buf[p->cur], p->nx, p->ny, p->nz,
+                                      p->pitch, p->d_scale + slot * p->nz, p->d_amax + slot * p->nz, p->stream);
+        if (e == cudaSuccess)
+            e = launch_pack16(p->storage, p->staging[0], p->staging[1], p->dbuf, p->nx, p->ny, p->nz, p->pitch,
+                              p->d_scale_d + slot * p->nz, p->d_amax_d + slot * p->nz, p->stream);
+        if (e != cudaSuccess) return fail_cuda(e, "field pack");
+        // the maxima of the levels the next two steps write start from zero
+        for (int64_t level = step + 1; level <= step + 2 && e == cudaSuccess; ++level) {
+            const int64_t sl = level % 4;
+            e = cudaMemsetAsync(p->d_amax + sl * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(p->d_amax_d + sl * p->nz, 0, sizeof(unsigned) * p->nz, p->stream);
         }
+        if (e != cudaSuccess) return fail_cuda(e, "amax reset");
     }
     cudaError_t e = cudaMemcpyAsync(p->d_step, &step, sizeof step, cudaMemcpyHostToDevice, p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "step counter copy");

@@ -55,13 +55,20 @@ struct Plan {
     int64_t field_elems = 0;
     int storage = STENCIL_FP32;
     int esize = 4;                        // bytes per wavefield element
-    void *buf[2] = {nullptr, nullptr};    // buf[cur] = u^n, buf[cur ^ 1] = u^{n-1}
+    // FP32: buf[cur] = u^n, buf[cur ^ 1] = u^{n-1} (overwritten by u^{n+1});
+    // 16-bit: buf[cur] = u^n, buf[cur ^ 1] receives u^{n+1}, and dbuf holds
+    // d^n = u^n - u^{n-1} (rewritten in place by each step)
+    void *buf[2] = {nullptr, nullptr};
+    void *dbuf = nullptr;
     bool user_owned = false;              // buf and kappa belong to the caller (not freed)
     float *kappa = nullptr;
     float *staging[2] = {nullptr, nullptr};   // 16-bit storage: FP32 copies for state transfer
-    float *d_scale = nullptr;             // 16-bit storage: [4][nz] per-plane scales by level mod 4
-    unsigned *d_amax = nullptr;           // 16-bit storage: [4][nz] per-plane max |u| by level mod 4
-    float growth = 0, src_bound = 0;
+    // 16-bit storage: [4][nz] per-plane scales and max |.| by level mod 4, of u and of d
+    float *d_scale = nullptr;
+    unsigned *d_amax = nullptr;
+    float *d_scale_d = nullptr;
+    unsigned *d_amax_d = nullptr;
+    float growth = 0, src_bound = 0;      // kappa_max * 3W; |source amplitude|
     int cur = 0;
     void *d_scratch = nullptr;
     int64_t *d_step = nullptr;
@@ -110,6 +117,13 @@ struct Plan {
     cudaError_t dev_alloc(void **ptr, size_t bytes);
     void dev_free(void *ptr);
     char *bptr(int b, int64_t off_elems) const { return static_cast<char *>(buf[b]) + off_elems * esize; }
+    // what the sweep reads beside kappa, point by point, when u^n is in
+    // buf[parity]: u^{n-1} (FP32) or d^n (16-bit)
+    char *aux_ptr(int parity, int64_t off_elems) const
+    {
+        return storage == STENCIL_FP32 ? bptr(parity ^ 1, off_elems)
+                                       : static_cast<char *>(dbuf) + off_elems * esize;
+    }
     int ensure_staging();
     // FP32 view of level n - which (the field itself for FP32 storage, an
     // unpacked copy in staging[which] for 16-bit storage); enqueued on stream

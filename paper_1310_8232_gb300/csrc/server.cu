@@ -58,8 +58,10 @@ int64_t projected_bytes(const stencil_desc &d)
 {
     const int esize = d.storage == STENCIL_FP32 ? 4 : 2;
     const int64_t elems = row_pitch(d.nx, esize) * d.ny * d.nz;
+    // two wavefield levels and kappa; 16-bit storage adds the difference
+    // field, its FP32 staging for the final read-back and the scale tables
     int64_t b = elems * (2 * esize + 4) + 64 * 1024 + 32LL * d.nz;
-    if (d.storage != STENCIL_FP32) b += 2 * elems * 4;      // FP32 staging for the final read-back
+    if (d.storage != STENCIL_FP32) b += elems * esize + 2 * elems * 4 + 64LL * d.nz;
     return b;
 }
 
@@ -531,8 +533,10 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
     }
     size_t free_b = 0, total_b = 0;
     if ((e = cudaMemGetInfo(&free_b, &total_b)) != cudaSuccess) return fail_cuda(e, "cudaMemGetInfo");
+    // a share of the memory free now, not of the device's total: on a GPU
+    // that other work also uses, the budget stays within what exists
     s->budget = cfg->hbm_budget_bytes > 0 ? cfg->hbm_budget_bytes
-                                          : (int64_t)(cfg->hbm_budget_frac * (double)total_b);
+                                          : (int64_t)(cfg->hbm_budget_frac * (double)free_b);
     stencil_tile t = cfg->tile;
     if (t.kernel == STENCIL_KERNEL_AUTO) t = stencil_tile{STENCIL_KERNEL_TILED, 64, 16, 0};
     if (t.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EUNSUPPORTED, "the server runs the tiled kernel");

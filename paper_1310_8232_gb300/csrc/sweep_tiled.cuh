@@ -29,13 +29,26 @@
 // the whole block leaves at the next barrier, after the copies it issued
 // have landed (also bounded).
 //
-// 16-bit storage: a stored value h of plane z at level n means h * s_n[z],
-// s a power of two (so scaling is exact).  The scale of each output plane
-// is fixed before anything is written, from a bound every block computes the
-// same way: |u^{n+1}| <= g * max|u^n| over planes z-R..z+R + max|u^{n-1}|
-// at z (+ the source amplitude on the source plane), g = 2 + kappa_max * 3W,
+// 16-bit storage (difference form): the state is u^n and the difference
+// d^n = u^n - u^{n-1}, both in 16 bits; one step is
+//     d^{n+1} = d^n + kappa Lambda(u^n) (+ source),   u^{n+1} = u^n + d^{n+1}
+// in FP32, the same update as 2 u^n - u^{n-1} + kappa Lambda(u^n) in exact
+// arithmetic.  Storing d instead of u^{n-1} keeps the step-to-step change at
+// the format's full relative precision: with u^{n-1} stored, the difference
+// u^n - u^{n-1} (a few per cent of u where the wave is slow against dx/dt)
+// keeps only the few low bits that survive the cancellation, and each
+// rounding of u then acts as a velocity kick that the scheme integrates.
+// u^{n+1} goes to the second u buffer (its neighbours still read u^n), d is
+// rewritten in place.  A stored value h of plane z at level n means h *
+// s_n[z], s a power of two (so scaling is exact), one scale table for u and
+// one for d.  The scales of each output plane are fixed before anything is
+// written, from bounds every block computes the same way:
+//     |d^{n+1}| <= max|d^n| at z + kappa_max 3W max|u^n| over planes z-R..z+R
+//                  (+ the source amplitude on the source plane),
+//     |u^{n+1}| <= max|u^n| at z + that bound,
 // and the stored magnitudes are kept below 2^15.  Each block reduces
-// max|u^{n+1}| of its tile per plane and merges it with one atomicMax.
+// max|u^{n+1}| and max|d^{n+1}| of its tile per plane and merges them with
+// one atomicMax each.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -83,14 +96,22 @@ __device__ __forceinline__ void st4(__nv_bfloat16 *p, const float4 &v)
     *reinterpret_cast<uint2 *>(p) = u;
 }
 
-// Smallest power of two s >= 2^-126 with b / s <= 2^15 (1 for b == 0).
-__device__ __forceinline__ float pow2_scale(float b)
+// Smallest power of two s >= 2^-126 with b / s <= 2^15 (1 for b == 0), and
+// its reciprocal (exact: also a power of two).
+__device__ __forceinline__ void pow2_scale(float b, float &s, float &inv)
 {
-    if (!(b > 0.0f)) return 1.0f;
-    if (!isfinite(b)) return ldexpf(1.0f, 127);
-    int e;
-    frexpf(b, &e);                 // b = f * 2^e, f in [0.5, 1): b < 2^e
-    return ldexpf(1.0f, max(e - 15, -126));
+    int k = 0;                     // s = 2^k
+    if (b > 0.0f) {
+        if (isinf(b)) {
+            k = 127;
+        } else {
+            int e;
+            frexpf(b, &e);         // b = f * 2^e, f in [0.5, 1): b < 2^e
+            k = max(e - 15, -126);
+        }
+    }
+    s = ldexpf(1.0f, k);
+    inv = ldexpf(1.0f, -k);
 }
 
 template <int R, int TX, int TY, typename E>
@@ -119,9 +140,10 @@ struct TiledShape {
     static constexpr int P_OFF = SU * U_STAGE;
     static constexpr int K_OFF = P_OFF + SA * P_STAGE;
     static constexpr int SIG_OFF = K_OFF + SA * K_STAGE;
-    // 16-bit: scales of the planes entering the ring, of u^{n-1} and of the
-    // outputs, plus per-warp maxima (double-buffered by plane parity)
-    static constexpr int SIG_BYTES = F32 ? 0 : ((ZMAX + 2 * R) + 2 * ZMAX + 2 * (NT / 32)) * 4;
+    // 16-bit: u scales of the planes entering the ring, d scales of the
+    // outputs' level n, reciprocal u and d scales of the outputs' level n+1,
+    // plus per-warp maxima of u and d (double-buffered by plane parity)
+    static constexpr int SIG_BYTES = F32 ? 0 : ((ZMAX + 2 * R) + 3 * ZMAX + 4 * (NT / 32)) * 4;
     static constexpr int BAR_OFF = ((SIG_OFF + SIG_BYTES + 15) / 16) * 16;
     static constexpr int EN_OFF = BAR_OFF + (SU + SA) * 8;     // per-warp FP64 energy sums
     static constexpr int FLAG_OFF = EN_OFF + (NT / 32) * 8;
@@ -194,10 +216,11 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     unsigned char *su = smem;
     unsigned char *sp = smem + S::P_OFF;
     unsigned char *sk = smem + S::K_OFF;
-    float *sig_in = reinterpret_cast<float *>(smem + S::SIG_OFF);   // [ZMAX + 2R]: s_n of planes pz0 + j
-    float *sig_prev = sig_in + (S::ZMAX + 2 * R);                    // [ZMAX]: s_{n-1} of outputs z0 + j
-    float *sig_out = sig_prev + S::ZMAX;                             // [ZMAX]: s_{n+1} of outputs z0 + j
-    unsigned *wmax = reinterpret_cast<unsigned *>(sig_out + S::ZMAX);   // [2][NT/32]
+    float *sig_in = reinterpret_cast<float *>(smem + S::SIG_OFF);   // [ZMAX + 2R]: u scale, level n, planes pz0 + j
+    float *sig_dn = sig_in + (S::ZMAX + 2 * R);                      // [ZMAX]: d scale, level n, outputs z0 + j
+    float *inv_u = sig_dn + S::ZMAX;                                 // [ZMAX]: 1 / u scale, level n+1, outputs
+    float *inv_d = inv_u + S::ZMAX;                                  // [ZMAX]: 1 / d scale, level n+1, outputs
+    unsigned *wmax = reinterpret_cast<unsigned *>(inv_d + S::ZMAX);  // [2 parities][u, d][NT/32]
     uint64_t *full_u = reinterpret_cast<uint64_t *>(smem + S::BAR_OFF);
     uint64_t *full_a = full_u + S::SU;
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + S::FLAG_OFF);
@@ -233,37 +256,45 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
         for (int t = 0; t < S::SU && t < nin; ++t) issue_u(t);
         for (int ja = 0; ja < S::SA && ja < nout; ++ja) issue_a(ja);
     }
-    int slot_out = 0;                         // 16-bit: slot of level n+1 in scale/amax
+    int slot_out = 0;                         // 16-bit: slot of level n+1 in the scale / amax tables
     if constexpr (!S::F32) {
         // scales of this block's planes, and those of its outputs (every block
         // computes the same value; tile 0 of each z-chunk publishes them)
         const int64_t n = n_level;
-        const int s_n = (int)(n & 3), s_p = (int)((n + 3) & 3);
+        const int s_n = (int)(n & 3);
         slot_out = (int)((n + 1) & 3);
         const int s_clear = (int)((n + 2) & 3);
         const float *scale_n = p.scale + (int64_t)s_n * p.nz;
-        const float *scale_p = p.scale + (int64_t)s_p * p.nz;
+        const float *scale_dn = p.scale_d + (int64_t)s_n * p.nz;
         const unsigned *amax_n = p.amax + (int64_t)s_n * p.nz;
-        const unsigned *amax_p = p.amax + (int64_t)s_p * p.nz;
+        const unsigned *amax_dn = p.amax_d + (int64_t)s_n * p.nz;
         for (int j = tid; j < nin; j += S::NT) {
             const int z = pz0 + j;
             sig_in[j] = (z >= 0 && z < p.nz) ? scale_n[z] : 1.0f;
         }
         for (int j = tid; j < nout; j += S::NT) {
             const int o = z0 + j;
-            sig_prev[j] = scale_p[o];
+            sig_dn[j] = scale_dn[o];
             float m = 0.0f;
             for (int d = -R; d <= R; ++d)
                 if (o + d >= 0 && o + d < p.nz) m = fmaxf(m, __uint_as_float(amax_n[o + d]));
-            float b = p.growth * m + __uint_as_float(amax_p[o]);
-            if (p.src.on && o == p.src.z) b += p.src_bound;
-            const float sg = pow2_scale(b);
-            sig_out[j] = sg;
-            if (bx == 0 && by == 0) p.scale[(int64_t)slot_out * p.nz + o] = sg;
+            float bd = p.growth * m + __uint_as_float(amax_dn[o]);
+            if (p.src.on && o == p.src.z) bd += p.src_bound;
+            const float bu = __uint_as_float(amax_n[o]) + bd;
+            float su, sd;
+            pow2_scale(bu, su, inv_u[j]);
+            pow2_scale(bd, sd, inv_d[j]);
+            if (bx == 0 && by == 0) {
+                p.scale[(int64_t)slot_out * p.nz + o] = su;
+                p.scale_d[(int64_t)slot_out * p.nz + o] = sd;
+            }
         }
-        // level n-2's slot becomes level n+2's: clear it for the next step
+        // level n-2's slots become level n+2's: clear them for the next step
         if (bx == 0 && by == 0 && z0 == 0)
-            for (int z = tid; z < p.nz; z += S::NT) p.amax[(int64_t)s_clear * p.nz + z] = 0u;
+            for (int z = tid; z < p.nz; z += S::NT) {
+                p.amax[(int64_t)s_clear * p.nz + z] = 0u;
+                p.amax_d[(int64_t)s_clear * p.nz + z] = 0u;
+            }
     }
     __syncthreads();
 
@@ -274,7 +305,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     const bool x_ok = gx < p.nx;
     const int own = (R + ty0) * S::BW + S::HX + 4 * tx4;   // own 4 points of row 0 in a u stage (elements)
     const int own_a = ty0 * TX + 4 * tx4;
-    E *dst = static_cast<E *>(p.up) + (int64_t)gy0 * p.pitch + gx;
+    E *dst = static_cast<E *>(p.up) + (int64_t)gy0 * p.pitch + gx;          // u^{n+1}
+    E *dst_d = S::F32 ? nullptr : static_cast<E *>(p.dv) + (int64_t)gy0 * p.pitch + gx;   // 16-bit: d^{n+1}
     const int src_row = p.src.y - gy0;                     // this thread's row holding the source, if any
     const bool src_here = p.src.on && (unsigned)src_row < (unsigned)S::ROWS && (unsigned)(p.src.x - gx) < 4u &&
                           p.src.z >= z0 && p.src.z < z1;
@@ -302,6 +334,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     int done = 0;                           // planes fully processed (block-uniform)
 
     if constexpr (!SPLIT) {
+        // FP32 storage: the ring rotated by unrolling over its R+1 slots
+        static_assert(S::F32, "the unrolled ring loop is the FP32 path");
         int su_stage = 0, su_phase = 0;     // stage / parity of plane i
         int sa_stage = 0, sa_phase = 0;     // aux stage / parity of output ja = i - 2R
         for (int i0 = 0; i0 < nin; i0 += S::RING) {
@@ -313,9 +347,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 if (i >= nin) return;                           // block-uniform
                 if (!mbar_wait(&full_u[su_stage], su_phase, p.err, wait_limit)) *abort_flag = 1;
                 const E *pl = reinterpret_cast<const E *>(su + su_stage * S::U_STAGE) + own;
-                const float sgi = S::F32 ? 1.0f : sig_in[i];
                 // column of the thread's x group: rows -R .. ROWS-1+R around row 0
-                // (stored units; scaled to true values where they enter the sums)
                 float4 col[S::ROWS + 2 * R];
 #pragma unroll
                 for (int h = 0; h < S::ROWS; ++h) col[R + h] = ld4(pl + h * S::BW);
@@ -338,7 +370,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float4 c = col[R + h];
                         float2 aA = __fmul2_rn(c0x3, lo2(c));
                         float2 aB = __fmul2_rn(c0x3, hi2(c));
-                        float2 zA = make_float2(0.f, 0.f), zB = make_float2(0.f, 0.f);   // 16-bit: z terms
                         // row[m] = u[gx - 8 + m], m = 0..19; own points are m = 8..11
                         float row[20];
                         {
@@ -369,29 +400,14 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             sA = __fadd2_rn(sA, __fadd2_rn(lo2(ym), lo2(yp)));
                             sB = __fadd2_rn(sB, __fadd2_rn(hi2(ym), hi2(yp)));
                             const float2 cr = make_float2(wf<R>(r), wf<R>(r));
-                            if constexpr (S::F32) {
-                                sA = __fadd2_rn(sA, lo2(zm));
-                                sB = __fadd2_rn(sB, hi2(zm));
-                            } else {
-                                zA = __ffma2_rn(cr, lo2(zm), zA);
-                                zB = __ffma2_rn(cr, hi2(zm), zB);
-                            }
+                            sA = __fadd2_rn(sA, lo2(zm));
+                            sB = __fadd2_rn(sB, hi2(zm));
                             aA = __ffma2_rn(cr, sA, aA);
                             aB = __ffma2_rn(cr, sB, aB);
-                        }
-                        if constexpr (!S::F32) {
-                            // stored units -> true values: (x, y, centre) * s_n + z terms
-                            const float2 ss = make_float2(sgi, sgi);
-                            aA = __ffma2_rn(ss, aA, zA);
-                            aB = __ffma2_rn(ss, aB, zB);
                         }
                         nA[h] = aA;
                         nB[h] = aB;
                     }
-                }
-                if constexpr (!S::F32) {
-#pragma unroll
-                    for (int h = 0; h < S::ROWS; ++h) col[R + h] = scale4(col[R + h], sgi);
                 }
                 if (++su_stage == S::SU) {
                     su_stage = 0;
@@ -414,12 +430,10 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     const float2 cR = make_float2(wf<R>(R), wf<R>(R));
                     const int ja = i - 2 * R;
                     if (!mbar_wait(&full_a[sa_stage], sa_phase, p.err, wait_limit)) *abort_flag = 1;
-                    const float sgp = S::F32 ? 1.0f : sig_prev[ja];
                     float4 prev[S::ROWS], kap[S::ROWS];
 #pragma unroll
                     for (int h = 0; h < S::ROWS; ++h) {
                         prev[h] = ld4(reinterpret_cast<const E *>(sp + sa_stage * S::P_STAGE) + own_a + h * TX);
-                        if constexpr (!S::F32) prev[h] = scale4(prev[h], sgp);
                         kap[h] = ld4(reinterpret_cast<const float *>(sk + sa_stage * S::K_STAGE) + own_a + h * TX);
                     }
                     if (++sa_stage == S::SA) {
@@ -427,8 +441,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         sa_phase ^= 1;
                     }
                     const int o = z0 + ja;
-                    const float inv_out = S::F32 ? 1.0f : 1.0f / sig_out[ja];   // exact: a power of two
-                    float omax = 0.0f;
 #pragma unroll
                     for (int h = 0; h < S::ROWS; ++h) {
                         const float4 c = col[R + h];
@@ -470,19 +482,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             epot = __ffma2_rn(uA, fA, epot);
                             epot = __ffma2_rn(uB, fB, epot);
                         }
-                        if constexpr (!S::F32) {
-                            if (ok)
-                                omax = fmaxf(omax, fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)),
-                                                         fmaxf(fabsf(nxt.z), fabsf(nxt.w))));
-                            nxt = scale4(nxt, inv_out);
-                        }
                         if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
                     }
-                    if constexpr (!S::F32) {
-                        const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
-                        if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
-                    }
-
                 }
                 // slot K held plane i - R - 1, which nothing needs any more
 #pragma unroll
@@ -502,13 +503,6 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 if (tid == 0) {
                     if (i + S::SU < nin) issue_u(i + S::SU);
                     if (i >= 2 * R && i - 2 * R + S::SA < nout) issue_a(i - 2 * R + S::SA);
-                    if constexpr (!S::F32) {
-                        if (i >= 2 * R) {
-                            unsigned m = 0;
-                            for (int w = 0; w < S::NT / 32; ++w) m = max(m, wmax[(i & 1) * (S::NT / 32) + w]);
-                            if (m) atomicMax(p.amax + (int64_t)slot_out * p.nz + z0 + (i - 2 * R), m);
-                        }
-                    }
                 }
             };
             Unroll<0, S::RING>::run(body);
@@ -527,6 +521,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
         // that name ring registers (z terms, the completed output, the ring
         // store) are instantiated per slot.  The loop body stays a fraction
         // of the fully unrolled one, which keeps the instruction fetch ahead.
+        static_assert(!S::F32, "the dispatched ring loop is the 16-bit difference-form path");
         float2 ekin = make_float2(0.f, 0.f);        // REC: energy terms of the current group of RING planes
         float2 epot = make_float2(0.f, 0.f);
         int k = 0;                                  // ring slot of plane i (i mod RING)
@@ -534,7 +529,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
         for (int i = 0; i < nin; ++i) {
             if (!mbar_wait(&full_u[i & 3], (i >> 2) & 1, p.err, wait_limit)) *abort_flag = 1;
             const E *pl = reinterpret_cast<const E *>(su + (i & 3) * S::U_STAGE) + own;
-            const float sgi = S::F32 ? 1.0f : sig_in[i];
+            const float sgi = sig_in[i];
             float4 col[S::ROWS + 2 * R];
 #pragma unroll
             for (int h = 0; h < S::ROWS; ++h) col[R + h] = ld4(pl + h * S::BW);
@@ -593,29 +588,26 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     xB[h] = aB;
                 }
             }
-            if constexpr (!S::F32) {
 #pragma unroll
-                for (int h = 0; h < S::ROWS; ++h) col[R + h] = scale4(col[R + h], sgi);
-            }
-            // u^{n-1} and kappa of output i - R, completed by this plane
+            for (int h = 0; h < S::ROWS; ++h) col[R + h] = scale4(col[R + h], sgi);
+            // d^n and kappa of output i - R, completed by this plane
             const bool fin = i >= 2 * R;
-            const E *aux_p = nullptr;
+            const E *aux_d = nullptr;
             const float *aux_k = nullptr;
-            float sgp = 1.0f, inv_out = 1.0f;
+            float sgd = 1.0f, iu = 1.0f, id = 1.0f;
             int o = 0;
             if (fin) {
                 const int ja = i - 2 * R;
                 if (!mbar_wait(&full_a[ja & 3], (ja >> 2) & 1, p.err, wait_limit)) *abort_flag = 1;
-                aux_p = reinterpret_cast<const E *>(sp + (ja & 3) * S::P_STAGE) + own_a;
+                aux_d = reinterpret_cast<const E *>(sp + (ja & 3) * S::P_STAGE) + own_a;
                 aux_k = reinterpret_cast<const float *>(sk + (ja & 3) * S::K_STAGE) + own_a;
-                if constexpr (!S::F32) {
-                    sgp = sig_prev[ja];
-                    inv_out = 1.0f / sig_out[ja];   // exact: a power of two
-                }
+                sgd = sig_dn[ja];
+                iu = inv_u[ja];
+                id = inv_d[ja];
                 o = z0 + ja;
             }
             const bool src_plane = src_here && o == p.src.z && fin;   // this thread adds the source now
-            float omax = 0.0f;
+            float umax = 0.0f, dmax = 0.0f;
             auto ring = [&](auto kc) {
                 constexpr int K = decltype(kc)::value;          // slot of plane i
                 constexpr int KF = (K + 1) % S::RING;           // slot of plane i - R
@@ -637,30 +629,28 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float2 cR = make_float2(wf<R>(R), wf<R>(R));
                         const float2 fA = __ffma2_rn(cR, lo2(c), pa[h][KF]);
                         const float2 fB = __ffma2_rn(cR, hi2(c), pb[h][KF]);
-                        const float4 cc = uq[h][KF];
-                        float4 prev = ld4(aux_p + h * TX);
-                        if constexpr (!S::F32) prev = scale4(prev, sgp);
+                        const float4 cc = uq[h][KF];                      // u^n
+                        const float4 dn = scale4(ld4(aux_d + h * TX), sgd);   // d^n
                         const float4 kap = ld4(aux_k + h * TX);
-                        // u^{n+1} = kappa * Lambda + (2 u^n - u^{n-1})
-                        const float2 oA =
-                            __ffma2_rn(lo2(kap), fA, __ffma2_rn(neg1, lo2(prev), __fmul2_rn(two, lo2(cc))));
-                        const float2 oB =
-                            __ffma2_rn(hi2(kap), fB, __ffma2_rn(neg1, hi2(prev), __fmul2_rn(two, hi2(cc))));
-                        float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
-                        if constexpr (ABS)
-                            absorb4(p.absorb_w, p.absorb_tab, p.nx, p.ny, p.nz, gx, gy0 + h, o, nxt, prev);
+                        // d^{n+1} = d^n + kappa * Lambda (+ source), u^{n+1} = u^n + d^{n+1}
+                        const float2 eA = __ffma2_rn(lo2(kap), fA, lo2(dn));
+                        const float2 eB = __ffma2_rn(hi2(kap), fB, hi2(dn));
+                        float4 dnx = make_float4(eA.x, eA.y, eB.x, eB.y);
                         if (src_plane && src_row == h) {
                             const int q = p.src.x - gx;
-                            if (q == 0) nxt.x += src_add;
-                            else if (q == 1) nxt.y += src_add;
-                            else if (q == 2) nxt.z += src_add;
-                            else nxt.w += src_add;
+                            if (q == 0) dnx.x += src_add;
+                            else if (q == 1) dnx.y += src_add;
+                            else if (q == 2) dnx.z += src_add;
+                            else dnx.w += src_add;
                         }
+                        const float2 oA = __fadd2_rn(lo2(cc), lo2(dnx));
+                        const float2 oB = __fadd2_rn(hi2(cc), hi2(dnx));
+                        const float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
                         const bool ok = x_ok && gy0 + h < p.ny;
                         if (REC && p.energy_on && ok) {
+                            // (u^{n+1} - u^n) = d^{n+1}: its square over kappa, and u^{n+1} Lambda(u^n)
                             float2 uA = lo2(nxt), uB = hi2(nxt);
-                            float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
-                            float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
+                            float2 dA = lo2(dnx), dB = hi2(dnx);
                             if (gx + 4 > p.nx) {
                                 const int nv = p.nx - gx;     // 1 .. 3
                                 if (nv < 2) uA.y = dA.y = 0.f;
@@ -674,13 +664,15 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             epot = __ffma2_rn(uA, fA, epot);
                             epot = __ffma2_rn(uB, fB, epot);
                         }
-                        if constexpr (!S::F32) {
-                            const float m =
-                                fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)), fmaxf(fabsf(nxt.z), fabsf(nxt.w)));
-                            omax = fmaxf(omax, ok ? m : 0.0f);
-                            nxt = scale4(nxt, inv_out);
+                        const float mu = fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)), fmaxf(fabsf(nxt.z), fabsf(nxt.w)));
+                        const float md = fmaxf(fmaxf(fabsf(dnx.x), fabsf(dnx.y)), fmaxf(fabsf(dnx.z), fabsf(dnx.w)));
+                        umax = fmaxf(umax, ok ? mu : 0.0f);
+                        dmax = fmaxf(dmax, ok ? md : 0.0f);
+                        if (ok) {
+                            const int64_t at = (int64_t)h * p.pitch + (int64_t)o * p.plane;
+                            st4(dst + at, scale4(nxt, iu));
+                            st4(dst_d + at, scale4(dnx, id));
                         }
-                        if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
                     }
                     // output i's partial: (centre, x, y) * s_n + z terms of
                     // planes i-1 .. i-R; slot K held plane i - R - 1, now free
@@ -704,10 +696,12 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 }
             };
             dispatch<S::RING>(k, ring);
-            if constexpr (!S::F32) {
-                if (fin) {
-                    const unsigned wm = __reduce_max_sync(0xffffffffu, __float_as_uint(omax));
-                    if ((tid & 31) == 0) wmax[(i & 1) * (S::NT / 32) + (tid >> 5)] = wm;
+            if (fin) {
+                const unsigned wu = __reduce_max_sync(0xffffffffu, __float_as_uint(umax));
+                const unsigned wd = __reduce_max_sync(0xffffffffu, __float_as_uint(dmax));
+                if ((tid & 31) == 0) {
+                    wmax[(i & 1) * 2 * (S::NT / 32) + (tid >> 5)] = wu;
+                    wmax[(i & 1) * 2 * (S::NT / 32) + (S::NT / 32) + (tid >> 5)] = wd;
                 }
             }
             if (REC && p.energy_on && (k == S::RING - 1 || i == nin - 1)) {
@@ -728,13 +722,17 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 if (i + S::SU < nin) issue_u(i + S::SU);
                 if (fin && i - 2 * R + S::SA < nout) issue_a(i - 2 * R + S::SA);
             }
-            if constexpr (!S::F32) {
-                // the plane's maximum, merged by the last warp (the first one issues the copies)
-                if (fin && tid == S::NT - 32) {
-                    unsigned m = 0;
-                    for (int w = 0; w < S::NT / 32; ++w) m = max(m, wmax[(i & 1) * (S::NT / 32) + w]);
-                    if (m) atomicMax(p.amax + (int64_t)slot_out * p.nz + z0 + (i - 2 * R), m);
+            // the plane's maxima, merged by the last warp (the first one issues the copies)
+            if (fin && tid == S::NT - 32) {
+                const unsigned *wm = wmax + (i & 1) * 2 * (S::NT / 32);
+                unsigned mu = 0, md = 0;
+                for (int w = 0; w < S::NT / 32; ++w) {
+                    mu = max(mu, wm[w]);
+                    md = max(md, wm[S::NT / 32 + w]);
                 }
+                const int64_t at = (int64_t)slot_out * p.nz + z0 + (i - 2 * R);
+                if (mu) atomicMax(p.amax + at, mu);
+                if (md) atomicMax(p.amax_d + at, md);
             }
         }
     }

@@ -193,7 +193,7 @@ static int make_view(const Plan *p, const Cand &c, int z0, int nzs, View *v)
         int rc = encode_map(&v->maps[par].u_halo, p->bptr(par, off), p->nx, p->ny, nzs, p->pitch, p->esize,
                             c.tx + 2 * info.hx, c.ty + 2 * p->R);
         if (!rc)
-            rc = encode_map(&v->maps[par].up_core, p->bptr(par ^ 1, off), p->nx, p->ny, nzs, p->pitch, p->esize,
+            rc = encode_map(&v->maps[par].up_core, p->aux_ptr(par, off), p->nx, p->ny, nzs, p->pitch, p->esize,
                             c.tx, c.ty);
         if (!rc) rc = encode_map(&v->maps[par].k_core, p->kappa + off, p->nx, p->ny, nzs, p->pitch, 4, c.tx, c.ty);
         if (rc) return rc;
@@ -208,6 +208,7 @@ static cudaError_t sweep_view(const Plan *p, const View &v, int parity, cudaStre
     prm.nz = v.nzs;
     prm.u = p->bptr(parity, off);
     prm.up = p->bptr(parity ^ 1, off);
+    if (p->storage != STENCIL_FP32) prm.dv = p->aux_ptr(parity, off);
     prm.kappa = p->kappa + off;
     prm.zchunk = std::min(v.c.zc, v.nzs);
     prm.src.on = 0;
@@ -425,8 +426,9 @@ int tune_plan(Plan *p, const stencil_desc *d)
     const size_t fbytes = (size_t)p->field_elems * p->esize;
     cudaError_t e = cudaMemsetAsync(p->buf[0], 0, fbytes, p->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->buf[1], 0, fbytes, p->stream);
-    if (e == cudaSuccess && p->d_scale) e = cudaMemsetAsync(p->d_scale, 0, sizeof(float) * 4 * p->nz, p->stream);
-    if (e == cudaSuccess && p->d_amax) e = cudaMemsetAsync(p->d_amax, 0, sizeof(unsigned) * 4 * p->nz, p->stream);
+    if (e == cudaSuccess && p->dbuf) e = cudaMemsetAsync(p->dbuf, 0, fbytes, p->stream);
+    // the four [4][nz] scale and max tables of u and d are contiguous
+    if (e == cudaSuccess && p->d_scale) e = cudaMemsetAsync(p->d_scale, 0, sizeof(float) * 16 * p->nz, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail_cuda(e, "clear after tuning");
     p->min_time_ms = min_ms;

@@ -1,10 +1,14 @@
-"""Reduced-precision storage (FP16 / BF16 u and u_prev, one power-of-two
-scale per z plane and time level, FP32 arithmetic) against the FP64 oracle.
+"""Reduced-precision storage (FP16 / BF16 u^n and d^n = u^n - u^{n-1}, one
+power-of-two scale per z plane and time level, FP32 arithmetic) against the
+FP64 oracle.
 
 Bars: FP32 storage relative L2 <= 1e-5 after 100 steps; reduced-precision
-storage <= 5e-3.  FP16 meets 5e-3 at 50 and 100 steps of the 512^3 layered
-shot; BF16's 8-bit significand does not (its error is asserted only against
-a regression bound here and reported as it is)."""
+storage <= 5e-3.  FP16 meets 5e-3 at steps 50, 100 and 200 of the 512^3
+layered shot.  BF16's 8-bit significand cannot: each step rounds u once, and
+those roundings add up like a random walk whatever the encoding of the step's
+change; BF16 is held to that derived bound (``rw_bound``)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -31,8 +35,27 @@ def stream(torch):
     return torch.cuda.current_stream().cuda_stream
 
 
+def rw_bound(steps: int, mant_bits: int) -> float:
+    """Relative L2 error the difference form can reach after ``steps`` steps.
+
+    One round-to-nearest to ``mant_bits`` explicit significand bits has a
+    relative L2 error sigma = 2^-p / sqrt(12 E[m^2]) over significands m
+    log-uniform on [1, 2) (E[m^2] = 3 / (2 ln 2)).  Each step rounds u^{n+1}
+    and d^{n+1} once; a rounding of u is a displacement error that the
+    (energy-conserving) scheme carries without amplification, a rounding of d
+    a velocity error of the size of d's own rounding.  n steps of independent
+    roundings of the two add up to at most sqrt(2 n) sigma."""
+    sigma = 2.0 ** -mant_bits / math.sqrt(12.0 * 1.5 / math.log(2.0))
+    return math.sqrt(2.0 * steps) * sigma
+
+
+FP16_BITS, BF16_BITS = 10, 7
+
+
 @pytest.mark.parametrize("storage,eps", [(1, 2.0 ** -11), (2, 2.0 ** -8)])
-def test_set_get_roundtrip_is_one_rounding(env, storage, eps):
+def test_set_get_roundtrip(env, storage, eps):
+    """u^n comes back after one rounding; u^{n-1} = u^n - d^n after two (u^n
+    and d^n = 0.5 u^n, each within half an ulp): 3 eps relative."""
     torch, st = env
     nx, ny, nz = 70, 33, 21
     v = workloads.constant_velocity(nx, ny, nz, 2000.0)
@@ -50,7 +73,7 @@ def test_set_get_roundtrip_is_one_rounding(env, storage, eps):
         st.stencil_destroy(plan)
     rel = np.abs(got - u) / np.abs(u)
     assert np.max(rel) <= eps * (1 + 1e-6)
-    assert np.max(np.abs(prev - u * 0.5) / np.abs(u * 0.5)) <= eps * (1 + 1e-6)
+    assert np.max(np.abs(prev - u * 0.5) / np.abs(u * 0.5)) <= 3 * eps * (1 + 1e-6)
 
 
 @pytest.mark.parametrize("storage", [1, 2])
@@ -75,7 +98,7 @@ def test_small_grid_matches_oracle_and_tiles(env, storage):
             st.stencil_destroy(plan)
         outs.append(out)
         assert np.all(np.isfinite(out))
-        assert oracle.rel_l2(out, ref) <= (5e-3 if storage == 1 else 5e-2)
+        assert oracle.rel_l2(out, ref) <= (5e-3 if storage == 1 else rw_bound(30, BF16_BITS))
     assert len(outs) >= 3
 
 
@@ -133,9 +156,9 @@ def test_512_layered_shot_errors_at_50_100_200_steps(env):
         print(f"  {name}: " + ", ".join(f"step {s}: {e:.3e}" for s, e in errs.items()))
     assert table["fp32"][100] <= 1e-5
     assert table["fp32"][50] <= 1e-5 and table["fp32"][200] <= 2e-5
-    assert table["fp16"][50] <= 5e-3 and table["fp16"][100] <= 5e-3
-    assert table["fp16"][200] <= 2e-2          # regression bound; above the 5e-3 bar
-    assert table["bf16"][100] <= 2e-1          # regression bound only
+    for s in marks:
+        assert table["fp16"][s] <= min(5e-3, rw_bound(s, FP16_BITS)), (s, table["fp16"][s])
+        assert table["bf16"][s] <= rw_bound(s, BF16_BITS), (s, table["bf16"][s])
 
 
 def test_256_layered_shot_radius_4_errors(env):
@@ -159,14 +182,15 @@ def test_256_layered_shot_radius_4_errors(env):
             st.stencil_destroy(plan)
     print(f"\nrelative L2 vs FP64 oracle, 256^3 layered, R=4, 100 steps: {errs}")
     assert errs["fp32"] <= 1e-5
-    assert errs["fp16"] <= 5e-3
-    assert errs["bf16"] <= 2e-1
+    assert errs["fp16"] <= min(5e-3, rw_bound(T, FP16_BITS))
+    assert errs["bf16"] <= rw_bound(T, BF16_BITS)
 
 
 @pytest.mark.parametrize("storage", [1, 2])
 def test_energy_with_16bit_storage(env, storage):
     """The fused energy sum with 16-bit storage against the oracle's energy of
-    the stored (rounded) fields: equal within the storage's rounding."""
+    the stored (rounded) state: u^{n+1} and u^n = u^{n+1} - d^{n+1} as read
+    back; equal within the storage's rounding."""
     torch, st = env
     nx, ny, nz, R = 48, 40, 36, 5
     v = workloads.layered_velocity(nx, ny, nz, seed=81)
@@ -177,15 +201,14 @@ def test_energy_with_16bit_storage(env, storage):
     try:
         st.stencil_set_fields(plan, u0, u0, 0)
         st.stencil_record_start(plan, energy=True, capacity=steps)
-        prev = np.empty_like(v)
-        st.stencil_get_field(plan, 0, prev)
         want = []
         for _ in range(steps):
             st.stencil_step(plan, 1)
             u = np.empty_like(v)
+            prev = np.empty_like(v)
             st.stencil_get_field(plan, 0, u)
+            st.stencil_get_field(plan, 1, prev)
             want.append(oracle.energy(v, workloads.DX, dt, R, u, prev))
-            prev = u
         got = np.empty(steps)
         assert st.stencil_record_read(plan, energy=got) == steps
     finally:

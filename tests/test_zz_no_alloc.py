@@ -72,10 +72,36 @@ def test_noalloc_reads_pitched_rows(env):
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch(env):
+    """2^28 + 2^20 elements, one block of partials more than the static array
+    holds: refused.  The buffers have the declared sizes (1.1 GB FP32, 2.2 GB
+    FP64), so even a launch that got past the check would stay in bounds."""
     torch, st = env
-    t = torch.zeros(4, dtype=torch.float32, device="cuda")
-    d = torch.zeros(4, dtype=torch.float64, device="cuda")
-    with pytest.raises(st.StencilError) as ei:
-        st.stencil_sqdiff_noalloc(t, 1024, d, 1024, 1024, 257, d)    # 2^28 + 2^20 elements
-    assert ei.value.code == st.STENCIL_EINVAL
-    assert "2^28" in str(ei.value)
+    nx, ny, nz = 1024, 1024, 257
+    t = torch.zeros(nx * ny * nz, dtype=torch.float32, device="cuda")
+    d = torch.zeros(nx * ny * nz, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    try:
+        with pytest.raises(st.StencilError) as ei:
+            st.stencil_sqdiff_noalloc(t, nx, d, nx, ny, nz, out)
+        assert ei.value.code == st.STENCIL_EINVAL
+        assert "2^28" in str(ei.value)
+    finally:
+        del t, d
+        torch.cuda.empty_cache()
+
+
+def test_noalloc_binding_checks_types_and_sizes(env):
+    """The bare C entry point cannot see buffer sizes: the binding refuses
+    wrong dtypes and buffers too small for the stated grid before calling it."""
+    torch, st = env
+    nx, ny, nz = 16, 8, 4
+    a = torch.zeros(nx * ny * nz, dtype=torch.float32, device="cuda")
+    b = torch.zeros(nx * ny * nz, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    for args in ((a.double(), nx, b, out), (a, nx, b.float(), out), (a, nx, b, out[:1]),
+                 (a[:-1], nx, b, out), (a, nx + 1, b, out), (a, nx - 1, b, out), (a, nx, b[:-1], out)):
+        with pytest.raises(ValueError):
+            st.stencil_sqdiff_noalloc(args[0], args[1], args[2], nx, ny, nz, args[3])
+    st.stencil_sqdiff_noalloc(a, nx, b, nx, ny, nz, out)
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == [0.0, 0.0]
