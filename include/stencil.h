@@ -64,15 +64,23 @@ extern "C" {
 /* ---- enums ----------------------------------------------------------- */
 typedef enum {
     STENCIL_FP32 = 0,   /* u, u_prev stored in FP32 */
-    STENCIL_FP16 = 1,   /* u, u_prev stored in FP16 with a per-z-plane FP32 scale */
-    STENCIL_BF16 = 2    /* u, u_prev stored in BF16 with a per-z-plane FP32 scale */
+    STENCIL_FP16 = 1,   /* u and d = u - u_prev stored in FP16, each with per-z-plane FP32 scales */
+    STENCIL_BF16 = 2    /* u and d = u - u_prev stored in BF16, each with per-z-plane FP32 scales */
 } stencil_storage;
 
 typedef enum {
     STENCIL_KERNEL_AUTO  = 0,  /* library default: the naive kernel for FP32 grids of at most 2^20
                                   points (latency-bound), else the tiled kernel, default tile */
     STENCIL_KERNEL_NAIVE = 1,  /* one thread per point, neighbours straight from global memory */
-    STENCIL_KERNEL_TILED = 2   /* 2.5D blocking: TMA-staged xy tile + halo, z-marching register queue */
+    STENCIL_KERNEL_TILED = 2,  /* 2.5D blocking: TMA-staged xy tile + halo, z-marching register queue */
+    STENCIL_KERNEL_TWO_STEP = 3 /* two time steps per sweep (temporal blocking, the "3.5D" blocking
+                                  of the paper's related work, Sec. 4): the first step on the tile
+                                  plus a ring of R points, the second on the tile; 10 B of traffic
+                                  per point update instead of 16.  FP32 storage only, no absorbing
+                                  layer, recording, injection, tuning or caller-owned buffers
+                                  (STENCIL_EUNSUPPORTED); tile fixed at 64 x 16 (R = 4) or 64 x 14
+                                  (R = 5), tx and ty are ignored; an odd step count ends with one
+                                  step of the tiled kernel.  The plan holds four FP32 wavefields. */
 } stencil_kernel;
 
 /* Tile parameters of the tiled kernel, the GPU analogue of the paper's

@@ -40,7 +40,7 @@ STENCIL_ECANCELLED = -11
 SHOT_QUEUED, SHOT_RUNNING, SHOT_DONE, SHOT_FAILED = 0, 1, 2, 3
 
 STENCIL_FP32, STENCIL_FP16, STENCIL_BF16 = 0, 1, 2
-STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_TILED = 0, 1, 2
+STENCIL_KERNEL_AUTO, STENCIL_KERNEL_NAIVE, STENCIL_KERNEL_TILED, STENCIL_KERNEL_TWO_STEP = 0, 1, 2, 3
 (STENCIL_TUNE_NONE, STENCIL_TUNE_OWN, STENCIL_TUNE_MWMB, STENCIL_TUNE_OB, STENCIL_TUNE_MMMB,
  STENCIL_TUNE_MAMB, STENCIL_TUNE_EXHAUSTIVE) = range(7)
 

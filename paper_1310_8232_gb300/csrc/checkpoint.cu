@@ -87,8 +87,8 @@ int pieces(Plan *p, Piece out[6], int *n)
     int k = 0;
     // u^n, then u^{n-1} (FP32) or d^n (16-bit)
     for (int w = 0; w < 2; ++w)
-        out[k++] = {w == 0 ? p->bptr(p->cur, 0) : p->aux_ptr(p->cur, 0), (size_t)p->pitch * p->esize,
-                    (size_t)p->nx * p->esize, (size_t)p->ny * p->nz};
+        out[k++] = {static_cast<char *>(w == 0 || p->storage == STENCIL_FP32 ? p->level_buf(w) : p->dbuf),
+                    (size_t)p->pitch * p->esize, (size_t)p->nx * p->esize, (size_t)p->ny * p->nz};
     if (p->storage != STENCIL_FP32) {
         const size_t sb = sizeof(float) * p->nz, ab = sizeof(unsigned) * p->nz;
         out[k++] = {reinterpret_cast<char *>(p->d_scale + at), sb, sb, 1};

@@ -91,6 +91,27 @@ cudaError_t launch_tiled_f32(int R, int tx, int ty, const TiledMaps &m, const Sw
 cudaError_t launch_tiled_f16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
 cudaError_t launch_tiled_bf16(int R, int tx, int ty, const TiledMaps &m, const SweepParams &p, cudaStream_t s);
 
+// ---- K7: two time steps per sweep (FP32; tile 64 x 16 at R = 4, 64 x 14 at R = 5) ----
+struct TwoStepMaps {
+    CUtensorMap u_halo;     // u^n, box (tx + 2 ex + 2 hx) x (ty + 4R) x 1
+    CUtensorMap up_region;  // u^{n-1}, box (tx + 2 ex) x (ty + 2R) x 1
+    CUtensorMap k_region;   // kappa, box (tx + 2 ex) x (ty + 2R) x 1
+    CUtensorMap u_core;     // u^n, box tx x ty x 1
+    CUtensorMap k_core;     // kappa, box tx x ty x 1
+};
+struct TwoStepInfo {
+    int smem;               // dynamic shared memory, bytes
+    int threads;            // block size
+    int ex;                 // ring of stage A around the tile, x columns on each side
+    int hx;                 // x halo of the u^n box beyond that ring
+};
+bool two_step_config(int R, int tx, int ty, TwoStepInfo *info);
+int two_step_tile_y(int R);
+int two_step_blocks_per_sm(int R);
+// u^{n+1} -> out1, u^{n+2} -> out2 (buffers other than the inputs)
+cudaError_t launch_two_step(int R, const TwoStepMaps &m, const SweepParams &p, float *out1, float *out2,
+                            cudaStream_t s);
+
 // grouped launch: one time step of every shot in `shots` (device array),
 // n_items blocks, block b doing items[b]; absorb: the variant with the
 // absorbing layer (FP32; shots without a layer pass through it unchanged)

@@ -118,11 +118,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw,
                int bh)
 {
+    return encode_map_strided(m, base, nx, ny, nz, pitch, pitch * ny, esize, bw, bh);
+}
+
+int encode_map_strided(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int64_t plane,
+                       int esize, int bw, int bh)
+{
     auto fn = encode_fn();
     if (!fn) return fail(STENCIL_ECUDA, "cuTensorMapEncodeTiled not available from the driver");
     const CUtensorMapDataType dt = esize == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
     cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    cuuint64_t strides[2] = {(cuuint64_t)(pitch * esize), (cuuint64_t)(pitch * ny * esize)};
+    cuuint64_t strides[2] = {(cuuint64_t)(pitch * esize), (cuuint64_t)(plane * esize)};
     cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -161,6 +167,7 @@ static cudaError_t read_small(void *dst, const void *src, size_t bytes, cudaStre
 // ---- plan internals -----------------------------------------------------------
 int Plan::build_maps()
 {
+    if (tile.kernel == STENCIL_KERNEL_TWO_STEP) return build_maps_two_step();
     if (tile.kernel != STENCIL_KERNEL_TILED) return STENCIL_OK;
     TiledInfo info;
     if (!tiled_config(R, storage, tile.tx, tile.ty, &info))
@@ -342,6 +349,7 @@ int Plan::enqueue(int nsteps)
 {
     if (nsteps < 0) return fail(STENCIL_EINVAL, "nsteps < 0");
     if (!velocity_ok) return fail(STENCIL_EINVAL, "the plan has no valid velocity model");
+    if (tile.kernel == STENCIL_KERNEL_TWO_STEP) return enqueue_two_step(nsteps);
     int left = nsteps;
     if (graph_len > 0 && left >= graph_len) {
         if (!graph_exec[0]) {
@@ -389,6 +397,9 @@ void Plan::release()
     }
     if (dbuf) dev_free(dbuf);
     dbuf = nullptr;
+    for (auto &b : tbuf)
+        if (b) dev_free(b);
+    tbuf[0] = tbuf[1] = nullptr;
     for (auto &b : staging)
         if (b) dev_free(b);
     staging[0] = staging[1] = nullptr;
@@ -470,7 +481,7 @@ int Plan::ensure_staging()
 int Plan::fp32_level(int which, const float **out)
 {
     if (storage == STENCIL_FP32) {
-        *out = static_cast<const float *>(buf[cur ^ which]);
+        *out = static_cast<const float *>(level_buf(which));
         return STENCIL_OK;
     }
     int rc = ensure_staging();
@@ -537,6 +548,31 @@ int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz)
     return best > 0 ? best : std::min(nz, zmax);
 }
 
+// The two-step kernel's z-chunk: the same block-scheduler model over its
+// one block per SM, each block also streaming the 4R extra planes of its two
+// stages (their stage A work weighs about as much as an output plane's).
+int choose_zchunk_two_step(int R, int nx, int ny, int nz)
+{
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    const int bps = std::max(1, two_step_blocks_per_sm(R));
+    const int ty = two_step_tile_y(R);
+    const int tiles = ((nx + 63) / 64) * ((ny + ty - 1) / ty);
+    static const int cand[] = {16, 24, 32, 48, 64, 96, 128, 192, 256};
+    int best = nz;
+    double best_t = predicted_makespan(2 * R, tiles, nz, nz, sms * bps);
+    for (int zc : cand) {
+        if (zc >= nz) break;
+        const double t = predicted_makespan(2 * R, tiles, nz, zc, sms * bps);
+        if (t < best_t) {
+            best_t = t;
+            best = zc;
+        }
+    }
+    return best;
+}
+
 stencil_tile default_tile(int R, int storage, int nx, int ny, int nz)
 {
     stencil_tile t;
@@ -601,6 +637,14 @@ int check_tile(int R, int storage, const stencil_tile &t)
         if (storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "the naive kernel stores FP32 only");
         return STENCIL_OK;
     }
+    if (t.kernel == STENCIL_KERNEL_TWO_STEP) {
+        if (storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "the two-step kernel stores FP32 only");
+        if (t.zchunk < 0) return fail(STENCIL_EINVAL, "zchunk must be >= 0");
+        TwoStepInfo info;
+        if (!two_step_config(R, t.tx, t.ty, &info))
+            return fail(STENCIL_EUNSUPPORTED, "two-step tile %dx%d not built for radius %d", t.tx, t.ty, R);
+        return STENCIL_OK;
+    }
     if (t.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EINVAL, "bad kernel id %d", t.kernel);
     if (t.zchunk < 0) return fail(STENCIL_EINVAL, "zchunk must be >= 0");
     TiledInfo info;
@@ -646,6 +690,13 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
         delete p;
         return fail(STENCIL_EUNSUPPORTED, "the absorbing layer needs FP32 storage");
     }
+    const bool two_step = d->tile.kernel == STENCIL_KERNEL_TWO_STEP && d->tune_mode == STENCIL_TUNE_NONE;
+    if (d->tile.kernel == STENCIL_KERNEL_TWO_STEP &&
+        (d->tune_mode != STENCIL_TUNE_NONE || p->absorb_w > 0 || p->user_owned || d->storage != STENCIL_FP32)) {
+        delete p;
+        return fail(STENCIL_EUNSUPPORTED,
+                    "the two-step kernel runs FP32 plans without tuning, absorbing layer or caller-owned buffers");
+    }
     auto bail = [&](int code) {
         p->release();
         delete p;
@@ -676,6 +727,13 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
         e = p->dev_alloc(&p->dbuf, fbytes);
         if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(difference field)"));
     }
+    if (two_step)
+        for (auto &b : p->tbuf) {
+            e = p->dev_alloc(&b, fbytes);
+            if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(two-step levels)"));
+            if ((e = cudaMemsetAsync(b, 0, fbytes, p->stream)) != cudaSuccess)
+                return bail(fail_cuda(e, "cudaMemsetAsync"));
+        }
     // scratch: step counter, error word, v range, reduction partials and
     // result, and (16-bit storage) the per-level per-plane scale and amax
     // tables of u and d, 4 x [4][nz] x 4 bytes
@@ -699,7 +757,7 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
         p->d_amax_d = reinterpret_cast<unsigned *>(sc + red_bytes + 3 * tab);
     }
     p->device_bytes = (p->user_owned ? 0 : 2 * (int64_t)fbytes + (int64_t)kbytes) + (int64_t)scratch +
-                      (p->dbuf ? (int64_t)fbytes : 0);
+                      (p->dbuf ? (int64_t)fbytes : 0) + (two_step ? 2 * (int64_t)fbytes : 0);
     if (p->absorb_w > 0) {
         // u^{n-1} of the layer's points, saved before each sweep
         p->absorb_shell = shell_points(d->nx, d->ny, d->nz, p->absorb_w);
@@ -753,6 +811,13 @@ int plan_create(const stencil_desc *d, Plan **out, cudaMemPool_t pool)
 
     // tile
     stencil_tile t = d->tile;
+    if (t.kernel == STENCIL_KERNEL_TWO_STEP) {
+        // fixed tile; the odd last step of a run uses the tiled kernel's 64 x 16
+        t.tx = 64;
+        t.ty = two_step_tile_y(d->radius);
+        if (t.zchunk < 0) t.zchunk = choose_zchunk_two_step(d->radius, d->nx, d->ny, d->nz);
+        p->t2_plain_zchunk = choose_zchunk(d->radius, STENCIL_FP32, 64, 16, d->nx, d->ny, d->nz);
+    }
     if (t.kernel == STENCIL_KERNEL_AUTO) t = default_tile(d->radius, d->storage, d->nx, d->ny, d->nz);
     else if (t.kernel == STENCIL_KERNEL_TILED && t.zchunk < 0)
         t.zchunk = choose_zchunk(d->radius, d->storage, t.tx, t.ty, d->nx, d->ny, d->nz);
@@ -885,7 +950,7 @@ int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, in
     // in FP32 (zeros where not given), then u^n and d^n = u^n - u^{n-1}
     // packed with the scales of level `step`.
     for (int k = 0; k < 2; ++k) {
-        float *dst = p->storage == STENCIL_FP32 ? static_cast<float *>(p->buf[p->cur ^ k]) : p->staging[k];
+        float *dst = p->storage == STENCIL_FP32 ? static_cast<float *>(p->level_buf(k)) : p->staging[k];
         cudaError_t e;
         if (!src[k])
             e = cudaMemsetAsync(dst, 0, (size_t)p->field_elems * sizeof(float), p->stream);
@@ -1021,7 +1086,8 @@ int stencil_debug_wait_fault(stencil_plan_t h, int32_t enable, uint32_t wait_ns)
     if (!h) return fail(STENCIL_EINVAL, "null plan");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
-    if (p->tile.kernel != STENCIL_KERNEL_TILED) return fail(STENCIL_EUNSUPPORTED, "the hook needs the tiled kernel");
+    if (p->tile.kernel != STENCIL_KERNEL_TILED && p->tile.kernel != STENCIL_KERNEL_TWO_STEP)
+        return fail(STENCIL_EUNSUPPORTED, "the hook needs the tiled or two-step kernel");
     int rc = p->check_device_error();
     if (rc) return rc;
     p->fault_tx = enable ? 16u : 0u;

@@ -17,10 +17,15 @@ int fail_cuda(cudaError_t e, const char *what);
 double cfl_limit(int R);
 int64_t row_pitch(int nx, int esize);
 int encode_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int esize, int bw, int bh);
+// the same with an explicit plane stride (elements), for a view of some rows
+// of every plane
+int encode_map_strided(CUtensorMap *m, const void *base, int nx, int ny, int nz, int64_t pitch, int64_t plane,
+                       int esize, int bw, int bh);
 // Grids of at most this many points get the naive kernel by default (FP32).
 constexpr int64_t NAIVE_MAX_POINTS = 1 << 20;
 stencil_tile default_tile(int R, int storage, int nx, int ny, int nz);
 int choose_zchunk(int R, int storage, int tx, int ty, int nx, int ny, int nz);
+int choose_zchunk_two_step(int R, int nx, int ny, int nz);
 int check_tile(int R, int storage, const stencil_tile &t);
 extern thread_local std::string g_last_error;
 
@@ -60,6 +65,13 @@ struct Plan {
     // d^n = u^n - u^{n-1} (rewritten in place by each step)
     void *buf[2] = {nullptr, nullptr};
     void *dbuf = nullptr;
+    // two-step kernel: two more FP32 levels; the levels live in one pair of
+    // the four buffers B = (buf[0], buf[1], tbuf[0], tbuf[1]), pair t2_pair:
+    // u^{n-1} = B[2 t2_pair], u^n = B[2 t2_pair + 1] (swapped when t2_swapped)
+    void *tbuf[2] = {nullptr, nullptr};
+    int t2_pair = 0;
+    bool t2_swapped = false;
+    int t2_plain_zchunk = 0;              // z-chunk of the one-step launches (64 x 16 tile)
     bool user_owned = false;              // buf and kappa belong to the caller (not freed)
     float *kappa = nullptr;
     float *staging[2] = {nullptr, nullptr};   // 16-bit storage: FP32 copies for state transfer
@@ -87,6 +99,10 @@ struct Plan {
     CUtensorMap maps_halo[2];
     CUtensorMap maps_core[2];
     CUtensorMap map_kcore;
+    // two-step kernel: its boxes of each of the four buffers, kappa's, and the
+    // one-step kernel's (64 x 16 tile) for an odd last step
+    CUtensorMap t2_u_halo[4], t2_up_region[4], t2_u_core[4], t2_plain_halo[4], t2_plain_core[4];
+    CUtensorMap t2_k_region, t2_k_core;
     int graph_len = 0;
     cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
     // recording (receiver traces, per-step energy); off when rec_mem is null
@@ -128,7 +144,16 @@ struct Plan {
     // FP32 view of level n - which (the field itself for FP32 storage, an
     // unpacked copy in staging[which] for 16-bit storage); enqueued on stream
     int fp32_level(int which, const float **out);
+    // the buffer holding u^{n - which} (which = 0, 1)
+    void *level_buf(int which) const;
     int build_maps();
+    // two-step kernel (plan_two_step.cu)
+    void *t2_buf(int k) const { return k < 2 ? buf[k] : tbuf[k - 2]; }
+    int build_maps_two_step();
+    cudaError_t launch_two_step_pair(int step_off, cudaStream_t s);
+    cudaError_t launch_two_step_single(int step_off, cudaStream_t s);
+    int enqueue_two_step(int nsteps);
+    int capture_graphs_two_step();
     int load_velocity(const float *v, int on_device);
     SweepParams params(int parity, int step_off) const;
     cudaError_t launch_one(int parity, int step_off, cudaStream_t s) const;

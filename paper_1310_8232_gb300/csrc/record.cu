@@ -51,6 +51,8 @@ int stencil_record_start(stencil_plan_t h, const stencil_record_cfg *c)
     if (!h || !c) return fail(STENCIL_EINVAL, "null argument");
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
+    if (p->tile.kernel == STENCIL_KERNEL_TWO_STEP)
+        return fail(STENCIL_EUNSUPPORTED, "the two-step kernel records nothing (each launch spans two steps)");
     if (c->capacity < 1) return fail(STENCIL_EINVAL, "capacity must be >= 1");
     if (c->receiver_z < -1 || c->receiver_z >= p->nz) return fail(STENCIL_EINVAL, "receiver_z outside the grid");
     if (c->receiver_y < -1 || c->receiver_y >= p->ny) return fail(STENCIL_EINVAL, "receiver_y outside the grid");

@@ -29,6 +29,8 @@ int stencil_inject_start(stencil_plan_t h, const stencil_inject_cfg *c)
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
     if (p->storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "injection needs FP32 storage");
+    if (p->tile.kernel == STENCIL_KERNEL_TWO_STEP)
+        return fail(STENCIL_EUNSUPPORTED, "the two-step kernel injects nothing (each launch spans two steps)");
     if (c->z < 0 || c->z >= p->nz) return fail(STENCIL_EINVAL, "injection plane outside the grid");
     if (c->y < -1 || c->y >= p->ny) return fail(STENCIL_EINVAL, "injection row outside the grid");
     if (c->steps < 1) return fail(STENCIL_EINVAL, "steps must be >= 1");

@@ -3,9 +3,11 @@
 // an exhaustive search and the library's own tuner.
 //
 // Mapping of the paper's roles onto one GPU:
-//   * "process on a core"  -> a CUDA stream sweeping its own z-slab of the
-//     grid (C streams share L2 and HBM the way the cores of a node share
-//     cache and memory bus);
+//   * "process on a core"  -> a CUDA stream sweeping its own slab of rows
+//     (a y-range of every plane, the grid's full depth: C streams share L2
+//     and HBM the way the cores of a node share cache and memory bus, and
+//     each meets the real run's z extent, so the z-chunk is judged in the
+//     setting it will run in);
 //   * "node"               -> a group; the nC candidates are split over N
 //     groups, which run one after another;
 //   * nI iterations        -> nI sweeps of the slab, timed with CUDA events
@@ -118,9 +120,7 @@ static const int TX_VALUES[] = {32, 64, 128};
 static const int TY_VALUES[] = {4, 8, 16, 32};
 
 // z-chunks 8, 12, 16, 24, 32, 48, ... (powers of two and 1.5x them) below
-// top, then top = min(nz, zmax) (zmax: the 16-bit kernels' bound; for the
-// slab-based selections the slab depth, since a chunk deeper than a slab
-// cannot be timed there)
+// top, then top = min(nz, zmax) (zmax: the 16-bit kernels' bound)
 static std::vector<int> zchunk_values(int nz, int zmax)
 {
     const int top = zmax > 0 ? std::min(nz, zmax) : nz;
@@ -153,9 +153,8 @@ static std::vector<Cand> admissible(int R, int storage, int nz)
     return out;
 }
 
-// The P-part candidate set of Sec. 3.7, one axis list per tile parameter;
-// z-chunks no deeper than `zcap` (the slab each selection stream sweeps).
-static std::vector<Cand> candidate_set(int R, int storage, int nz, int P, int zcap)
+// The P-part candidate set of Sec. 3.7, one axis list per tile parameter.
+static std::vector<Cand> candidate_set(int R, int storage, int nz, int P)
 {
     std::vector<int> txs(std::begin(TX_VALUES), std::end(TX_VALUES));
     std::vector<int> tys(std::begin(TY_VALUES), std::end(TY_VALUES));
@@ -163,39 +162,42 @@ static std::vector<Cand> candidate_set(int R, int storage, int nz, int P, int zc
     int zmax = 0;
     for (int tx : pick_axis(txs, P))
         for (int ty : pick_axis(tys, P))
-            if (feasible(R, storage, tx, ty, &zmax)) {
-                const int cap = zmax > 0 ? std::min(zmax, zcap) : zcap;
-                for (int zc : pick_axis(zchunk_values(nz, cap), P)) out.push_back({tx, ty, zc});
-            }
+            if (feasible(R, storage, tx, ty, &zmax))
+                for (int zc : pick_axis(zchunk_values(nz, zmax), P)) out.push_back({tx, ty, zc});
     return out;
 }
 
 // ---- timing engine ----------------------------------------------------------------
-// A view of the plan's buffers restricted to planes [z0, z0 + nzs), with the
-// tensor maps of one candidate tile.  Views of different slabs never touch
-// each other's memory, so several streams can sweep them at once.
+// A view of the plan's buffers restricted to rows [y0, y0 + nys) of every
+// plane (all nz planes), with the tensor maps of one candidate tile.  Views
+// of different row slabs never touch each other's memory, so several streams
+// can sweep them at once; each sweeps the grid's full depth, so a candidate
+// z-chunk meets the same number of planes (and warm-up planes per chunk) as
+// in the real run.
 struct View {
-    int z0 = 0, nzs = 0;
+    int y0 = 0, nys = 0;
     Cand c{};
     TiledMaps maps[2];   // by parity
 };
 
-static int make_view(const Plan *p, const Cand &c, int z0, int nzs, View *v)
+static int make_view(const Plan *p, const Cand &c, int y0, int nys, View *v)
 {
     TiledInfo info;
     if (!tiled_config(p->R, p->storage, c.tx, c.ty, &info))
         return fail(STENCIL_EUNSUPPORTED, "tile %dx%d unavailable", c.tx, c.ty);
-    v->z0 = z0;
-    v->nzs = nzs;
+    v->y0 = y0;
+    v->nys = nys;
     v->c = c;
-    const int64_t off = (int64_t)z0 * p->pitch * p->ny;
+    const int64_t off = (int64_t)y0 * p->pitch, plane = p->pitch * p->ny;
     for (int par = 0; par < 2; ++par) {
-        int rc = encode_map(&v->maps[par].u_halo, p->bptr(par, off), p->nx, p->ny, nzs, p->pitch, p->esize,
-                            c.tx + 2 * info.hx, c.ty + 2 * p->R);
+        int rc = encode_map_strided(&v->maps[par].u_halo, p->bptr(par, off), p->nx, nys, p->nz, p->pitch, plane,
+                                    p->esize, c.tx + 2 * info.hx, c.ty + 2 * p->R);
         if (!rc)
-            rc = encode_map(&v->maps[par].up_core, p->aux_ptr(par, off), p->nx, p->ny, nzs, p->pitch, p->esize,
-                            c.tx, c.ty);
-        if (!rc) rc = encode_map(&v->maps[par].k_core, p->kappa + off, p->nx, p->ny, nzs, p->pitch, 4, c.tx, c.ty);
+            rc = encode_map_strided(&v->maps[par].up_core, p->aux_ptr(par, off), p->nx, nys, p->nz, p->pitch, plane,
+                                    p->esize, c.tx, c.ty);
+        if (!rc)
+            rc = encode_map_strided(&v->maps[par].k_core, p->kappa + off, p->nx, nys, p->nz, p->pitch, plane, 4,
+                                    c.tx, c.ty);
         if (rc) return rc;
     }
     return STENCIL_OK;
@@ -203,14 +205,14 @@ static int make_view(const Plan *p, const Cand &c, int z0, int nzs, View *v)
 
 static cudaError_t sweep_view(const Plan *p, const View &v, int parity, cudaStream_t s)
 {
-    const int64_t off = (int64_t)v.z0 * p->pitch * p->ny;
+    const int64_t off = (int64_t)v.y0 * p->pitch;
     SweepParams prm = p->params(parity, 0);
-    prm.nz = v.nzs;
+    prm.ny = v.nys;                 // rows of the view; plane stride stays the grid's
     prm.u = p->bptr(parity, off);
     prm.up = p->bptr(parity ^ 1, off);
     if (p->storage != STENCIL_FP32) prm.dv = p->aux_ptr(parity, off);
     prm.kappa = p->kappa + off;
-    prm.zchunk = std::min(v.c.zc, v.nzs);
+    prm.zchunk = std::min(v.c.zc, p->nz);
     prm.src.on = 0;
     prm.energy_on = 0;              // selection sweeps time the plain sweep
     prm.fault_tx = 0;
@@ -270,18 +272,18 @@ static int time_together(const Plan *p, Streams &S, const std::vector<View> &vie
     return STENCIL_OK;
 }
 
-// Slab c of C: planes [c*nz/C, (c+1)*nz/C).
-static void slab(int nz, int C, int c, int *z0, int *n)
+// Slab c of C: rows [c*ny/C, (c+1)*ny/C) of every plane.
+static void slab(int ny, int C, int c, int *y0, int *n)
 {
-    const int a = (int)((int64_t)c * nz / C), b = (int)((int64_t)(c + 1) * nz / C);
-    *z0 = a;
+    const int a = (int)((int64_t)c * ny / C), b = (int)((int64_t)(c + 1) * ny / C);
+    *y0 = a;
     *n = b - a;
 }
 
 static int time_full(const Plan *p, Streams &S, const Cand &c, int nI, double *ms)
 {
     std::vector<View> v(1);
-    int rc = make_view(p, c, 0, p->nz, &v[0]);
+    int rc = make_view(p, c, 0, p->ny, &v[0]);
     if (rc) return rc;
     Streams one;
     if ((rc = one.init(1))) return rc;
@@ -298,14 +300,14 @@ int tune_plan(Plan *p, const stencil_desc *d)
     const int nI = d->tune.iterations > 0 ? d->tune.iterations : 8;
     int C = d->tune.streams > 0 ? d->tune.streams : 4;
     int G = d->tune.groups > 0 ? d->tune.groups : 2;
-    C = std::max(1, std::min(C, p->nz));
+    C = std::max(1, std::min(C, p->ny));
     Streams S;
     int rc = S.init(C);
     if (rc) return rc;
 
     std::vector<Cand> cands = (mode == STENCIL_TUNE_EXHAUSTIVE || mode == STENCIL_TUNE_OWN)
                                   ? admissible(p->R, p->storage, p->nz)
-                                  : candidate_set(p->R, p->storage, p->nz, P, std::max(1, p->nz / C));
+                                  : candidate_set(p->R, p->storage, p->nz, P);
     if (cands.empty()) return fail(STENCIL_EUNSUPPORTED, "no feasible tile");
     Cand chosen{};
     double min_ms = 0, actual_ms = 0;
@@ -324,9 +326,9 @@ int tune_plan(Plan *p, const stencil_desc *d)
                 const Cand &c = cands[(size_t)g * K + k];
                 std::vector<View> views(C);
                 for (int s = 0; s < C; ++s) {
-                    int z0, n;
-                    slab(p->nz, C, s, &z0, &n);
-                    if ((rc = make_view(p, c, z0, n, &views[s]))) return rc;
+                    int y0, n;
+                    slab(p->ny, C, s, &y0, &n);
+                    if ((rc = make_view(p, c, y0, n, &views[s]))) return rc;
                 }
                 std::vector<double> ms(C);
                 if ((rc = time_together(p, S, views, nI, ms.data()))) return rc;
@@ -345,10 +347,10 @@ int tune_plan(Plan *p, const stencil_desc *d)
         for (int k = 0; k < K; ++k) {
             std::vector<View> views(C);
             for (int s = 0; s < C; ++s) {
-                int z0, n;
-                slab(p->nz, C, s, &z0, &n);
+                int y0, n;
+                slab(p->ny, C, s, &y0, &n);
                 const Cand &c = cands[std::min<size_t>((size_t)s * K + k, cands.size() - 1)];
-                if ((rc = make_view(p, c, z0, n, &views[s]))) return rc;
+                if ((rc = make_view(p, c, y0, n, &views[s]))) return rc;
             }
             std::vector<double> ms(C);
             if ((rc = time_together(p, S, views, nI, ms.data()))) return rc;
@@ -403,9 +405,9 @@ int tune_plan(Plan *p, const stencil_desc *d)
     if (concurrent_verify) {
         std::vector<View> views(C);
         for (int s = 0; s < C; ++s) {
-            int z0, n;
-            slab(p->nz, C, s, &z0, &n);
-            if ((rc = make_view(p, chosen, z0, n, &views[s]))) return rc;
+            int y0, n;
+            slab(p->ny, C, s, &y0, &n);
+            if ((rc = make_view(p, chosen, y0, n, &views[s]))) return rc;
         }
         std::vector<double> ms(C);
         if ((rc = time_together(p, S, views, nI, ms.data()))) return rc;
