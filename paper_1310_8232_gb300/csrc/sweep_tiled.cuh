@@ -190,6 +190,11 @@ __device__ __forceinline__ void dispatch(int k, F &f)
 }
 
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+// 1 / max(kappa, FLT_MIN) for two points (the hardware reciprocal; energy sums only)
+__device__ __forceinline__ float2 rcp_kappa2(const float2 &k)
+{
+    return make_float2(rcp_approx(fmaxf(k.x, 1.17549435e-38f)), rcp_approx(fmaxf(k.y, 1.17549435e-38f)));
+}
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 scale4(const float4 &v, float s)
 {
@@ -332,6 +337,12 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     const float2 neg1 = make_float2(-1.0f, -1.0f);
     const float2 c0x3 = make_float2(3.0f * wf<R>(0), 3.0f * wf<R>(0));
     int done = 0;                           // planes fully processed (block-uniform)
+    // REC: this thread's energy terms, FP32 over each group of RING planes,
+    // then FP64 over the z-chunk; one warp sum at the end.  Points outside the
+    // grid add exactly zero: their u^{n+1} and u^n are zero (zero-filled
+    // inputs, kappa = 0 there), and 1/kappa is taken of max(kappa, FLT_MIN),
+    // which keeps 0 * (1/kappa) finite, so no point needs a mask.
+    double eacc = 0.0;
 
     if constexpr (!SPLIT) {
         // FP32 storage: the ring rotated by unrolling over its R+1 slots
@@ -462,27 +473,18 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             else if (k == 2) nxt.z += src_add;
                             else nxt.w += src_add;
                         }
-                        const bool ok = x_ok && gy0 + h < p.ny;
-                        if (REC && p.energy_on && ok) {
+                        if (REC && p.energy_on) {
                             // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa (into ekin) and
-                            // u^{n+1} Lambda(u^n) (into epot); points beyond nx count zero
-                            float2 uA = make_float2(nxt.x, nxt.y), uB = make_float2(nxt.z, nxt.w);
-                            float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
-                            float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
-                            if (gx + 4 > p.nx) {
-                                const int nv = p.nx - gx;     // 1 .. 3
-                                if (nv < 2) uA.y = dA.y = 0.f;
-                                if (nv < 3) uB.x = dB.x = 0.f;
-                                uB.y = dB.y = 0.f;
-                            }
-                            const float2 rA = make_float2(rcp_approx(kap[h].x), rcp_approx(kap[h].y));
-                            const float2 rB = make_float2(rcp_approx(kap[h].z), rcp_approx(kap[h].w));
-                            ekin = __ffma2_rn(__fmul2_rn(dA, dA), rA, ekin);
-                            ekin = __ffma2_rn(__fmul2_rn(dB, dB), rB, ekin);
+                            // u^{n+1} Lambda(u^n) (into epot)
+                            const float2 uA = lo2(nxt), uB = hi2(nxt);
+                            const float2 dA = __ffma2_rn(neg1, lo2(cc), uA);
+                            const float2 dB = __ffma2_rn(neg1, hi2(cc), uB);
+                            ekin = __ffma2_rn(__fmul2_rn(dA, dA), rcp_kappa2(lo2(kap[h])), ekin);
+                            ekin = __ffma2_rn(__fmul2_rn(dB, dB), rcp_kappa2(hi2(kap[h])), ekin);
                             epot = __ffma2_rn(uA, fA, epot);
                             epot = __ffma2_rn(uB, fB, epot);
                         }
-                        if (ok) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
+                        if (x_ok && gy0 + h < p.ny) st4(dst + (int64_t)h * p.pitch + (int64_t)o * p.plane, nxt);
                     }
                 }
                 // slot K held plane i - R - 1, which nothing needs any more
@@ -506,13 +508,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 }
             };
             Unroll<0, S::RING>::run(body);
-            if (REC && p.energy_on) {
-                // the warp's FP32 sum over these planes, added in FP64 by lane 0
-                float e = (ekin.x + ekin.y) - (epot.x + epot.y);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-                if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
-            }
+            if (REC && p.energy_on) eacc += (double)((ekin.x + ekin.y) - (epot.x + epot.y));
         }
     } else {
         // The same per-plane work with the ring slot chosen at run time.  The
@@ -647,22 +643,13 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float2 oB = __fadd2_rn(hi2(cc), hi2(dnx));
                         const float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
                         const bool ok = x_ok && gy0 + h < p.ny;
-                        if (REC && p.energy_on && ok) {
+                        if (REC && p.energy_on) {
                             // (u^{n+1} - u^n) = d^{n+1}: its square over kappa, and u^{n+1} Lambda(u^n)
-                            float2 uA = lo2(nxt), uB = hi2(nxt);
-                            float2 dA = lo2(dnx), dB = hi2(dnx);
-                            if (gx + 4 > p.nx) {
-                                const int nv = p.nx - gx;     // 1 .. 3
-                                if (nv < 2) uA.y = dA.y = 0.f;
-                                if (nv < 3) uB.x = dB.x = 0.f;
-                                uB.y = dB.y = 0.f;
-                            }
-                            const float2 rA = make_float2(rcp_approx(kap.x), rcp_approx(kap.y));
-                            const float2 rB = make_float2(rcp_approx(kap.z), rcp_approx(kap.w));
-                            ekin = __ffma2_rn(__fmul2_rn(dA, dA), rA, ekin);
-                            ekin = __ffma2_rn(__fmul2_rn(dB, dB), rB, ekin);
-                            epot = __ffma2_rn(uA, fA, epot);
-                            epot = __ffma2_rn(uB, fB, epot);
+                            const float2 dA = lo2(dnx), dB = hi2(dnx);
+                            ekin = __ffma2_rn(__fmul2_rn(dA, dA), rcp_kappa2(lo2(kap)), ekin);
+                            ekin = __ffma2_rn(__fmul2_rn(dB, dB), rcp_kappa2(hi2(kap)), ekin);
+                            epot = __ffma2_rn(lo2(nxt), fA, epot);
+                            epot = __ffma2_rn(hi2(nxt), fB, epot);
                         }
                         const float mu = fmaxf(fmaxf(fabsf(nxt.x), fabsf(nxt.y)), fmaxf(fabsf(nxt.z), fabsf(nxt.w)));
                         const float md = fmaxf(fmaxf(fabsf(dnx.x), fabsf(dnx.y)), fmaxf(fabsf(dnx.z), fabsf(dnx.w)));
@@ -705,11 +692,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 }
             }
             if (REC && p.energy_on && (k == S::RING - 1 || i == nin - 1)) {
-                // the warp's FP32 sum over the group's planes, added in FP64 by lane 0
-                float e = (ekin.x + ekin.y) - (epot.x + epot.y);
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-                if ((tid & 31) == 0) en_warp[tid >> 5] += (double)e;
+                eacc += (double)((ekin.x + ekin.y) - (epot.x + epot.y));
                 ekin = epot = make_float2(0.f, 0.f);
             }
             if (++k == S::RING) k = 0;
@@ -735,6 +718,12 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 if (md) atomicMax(p.amax_d + at, md);
             }
         }
+    }
+    if (REC && p.energy_on) {
+        // the warp's sum of its threads' FP64 energy terms (fixed order)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, off);
+        if ((tid & 31) == 0) en_warp[tid >> 5] = eacc;
     }
     if (*abort_flag && tid == 0) {
         // let the copies already issued land before the block's shared
