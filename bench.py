@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-timesteps", type=int, default=10)
+    ap.add_argument("--host-method", action="store_true",
+                    help="single: also time the paper's method on the host cores (FP32 blocked sweep, "
+                         "MWMB-selected block, P=3, nI=1) on the same grid")
     ap.add_argument("--workload", choices=["single", "batch", "serve", "rtm"], default="single",
                     help="single: one 512^3 shot; batch: 64 uneven shots in one grouped launch per step "
                          "vs a per-shot loop; serve: Poisson arrivals through the shot server")
@@ -194,6 +197,31 @@ def cpu_baseline(args, v, dt):
     return {"value": pts / el / 1e9, "unit": METRIC, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": f"first {steps} of {args.timesteps} time steps of the {args.n}^3 shot, "
                       f"FP64 unblocked oracle, {el:.1f} s"}
+
+
+def host_method_baseline(args, v, dt):
+    """The paper's method on this host's cores: MWMB (P = 3, nI = 1) picks the
+    block of an FP32 blocked sweep across the cores, which then runs the
+    first --cpu-timesteps steps of the same shot on the whole grid."""
+    import numpy as np
+
+    from oracle import host_method as hm
+    from paper_1310_8232_gb300 import workloads
+    n, R, steps = args.n, args.radius, args.cpu_timesteps
+    kap = hm.kappa(v, workloads.DX, dt)
+    t0 = time.perf_counter()
+    sel = hm.select_mwmb(kap, R, P=3, nI=1)
+    sel_s = time.perf_counter() - t0
+    u = np.zeros((n, n, n), np.float32)
+    up = np.zeros_like(u)
+    src = (n // 2, n // 2, n // 2)
+    scale = float(v[src[2], src[1], src[0]]) ** 2 * dt * dt
+    el = hm.run(kap, R, steps, u, up, src=src, src_scale=scale, dt=dt, block=sel["block"])
+    return {"value": float(n) ** 3 * steps / el / 1e9, "unit": METRIC, "cores": sel["cores"],
+            "kind": "paper method on the host: FP32 blocked sweep, block chosen by MWMB across the cores",
+            "block": list(sel["block"]), "candidates": sel["candidates"], "selection_s": sel_s,
+            "min_time_s": sel["min_time"], "actual_time_s": sel["actual_time"], "quality": sel["quality"],
+            "sample": f"first {steps} of {args.timesteps} time steps of the {n}^3 shot after the selection"}
 
 
 def run_reference(args):
@@ -628,6 +656,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args, v, dt)
+    host = None
+    if rank == 0 and world == 1 and args.host_method:
+        host = host_method_baseline(args, v, dt)
 
     if rank == 0:
         line = {
@@ -649,6 +680,7 @@ def main():
                                    "per-launch time = sum / launches (includes the step-counter kernel)"},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            **({"host_method": host} if host else {}),
             "gpu_launches": args.steps * launches_per_shot,
             "clocks": clk.summary(),
         }

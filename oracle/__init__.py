@@ -8,7 +8,9 @@ here imports the product package.
 The numerical work is in ``stencil_oracle.c`` (plain C, FP64, OpenMP only
 over independent k-blocks); this module builds it with gcc on first use and
 wraps it with ctypes.  ``selection.py`` holds the paper's blocksize-selection
-methodology (Sec. 3.2-3.7) in plain Python.
+methodology (Sec. 3.2-3.7) in plain Python.  ``host_method.py`` wraps
+``host_method.c``, the paper's method run on the host cores (an FP32 blocked
+sweep with an MWMB-selected block): a reported CPU baseline, not a checker.
 
 Arrays are numpy float64 of shape (nz, ny, nx), C order (x fastest).
 """
@@ -29,7 +31,10 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle into oracle/liboracle.so (gcc, -O2, no FP contraction)."""
+    """Compile the C oracle into oracle/liboracle.so (gcc, -O2, no FP contraction),
+    and the host-method baseline (host_method.c) beside it."""
+    from . import host_method
+    host_method.build(force)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
