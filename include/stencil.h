@@ -434,6 +434,38 @@ STENCIL_API int shot_server_create(const shot_server_cfg *cfg, shot_server_t *ou
  * exceeds the budget (it is recorded as FAILED). */
 STENCIL_API int shot_submit(shot_server_t s, const stencil_desc *d, int32_t nsteps, float *out_host,
                             uint64_t *ticket);
+/* A served reverse-time migration: the application the paper's kernel is
+ * the "3D model" step of (Sec. 2, Algorithm 1), with the readings of the
+ * single-plan migration (stencil_record_*, stencil_inject_*,
+ * stencil_image_accumulate).  The shot runs nsteps forward steps with its
+ * point source (and absorbing layer, if any), recording u on the receiver
+ * plane (or row) after every step and keeping u at the times t = k, 2k, ...,
+ * nsteps in device memory; then nsteps backward steps on the same model
+ * without the point source, the recorded traces injected on the receiver
+ * plane in reverse time order, adding image_scale * S(t) * r (the zero-lag
+ * cross-correlation of the snapshot of time t with the backward field that
+ * belongs to time t) at every snapshot time.  Both phases run in the shot's
+ * lane beside the other resident shots (the per-step record, injection,
+ * snapshot and imaging work in one small grouped kernel after each grouped
+ * sweep).  The image equals the single-plan migration's with the server's
+ * tile, bit for bit. */
+typedef struct {
+    int32_t receiver_z;     /* receiver plane, 0 <= z < nz */
+    int32_t receiver_y;     /* -1: every row of the plane; else that row */
+    int32_t snap_every;     /* k >= 1; nsteps must be a multiple of k */
+    float   image_scale;    /* default 1 */
+} shot_rtm_cfg;
+
+STENCIL_API void shot_rtm_cfg_init(shot_rtm_cfg *c);
+/* Queue a migration of nsteps forward + nsteps backward steps.  image_host:
+ * dense nx*ny*nz floats (required); traces_host: nsteps * rows * nx floats
+ * (rows = ny, or 1 for one receiver row) or NULL; both must stay valid until
+ * the shot is DONE or FAILED.  FP32 servers only (STENCIL_EUNSUPPORTED).  The
+ * shot's device bytes include nsteps / k snapshots, the traces and the image;
+ * STENCIL_EBUDGET if they alone exceed the budget.  shot_poll counts both
+ * phases' steps (2 nsteps in all). */
+STENCIL_API int shot_submit_rtm(shot_server_t s, const stencil_desc *d, int32_t nsteps, const shot_rtm_cfg *cfg,
+                                float *image_host, float *traces_host, uint64_t *ticket);
 /* State (shot_state) and timing of a shot; does not block. */
 STENCIL_API int shot_poll(shot_server_t s, uint64_t ticket, int32_t *state, shot_timing *t);
 /* Block until the shot is DONE or FAILED, or timeout_s passes (STENCIL_ENOTREADY). */

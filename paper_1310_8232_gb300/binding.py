@@ -113,6 +113,11 @@ class shot_server_cfg(ctypes.Structure):
     ]
 
 
+class shot_rtm_cfg(ctypes.Structure):
+    _fields_ = [("receiver_z", ctypes.c_int32), ("receiver_y", ctypes.c_int32),
+                ("snap_every", ctypes.c_int32), ("image_scale", ctypes.c_float)]
+
+
 class shot_timing(ctypes.Structure):
     _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
                 ("steps_done", ctypes.c_int64), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
@@ -172,6 +177,10 @@ _lib.shot_server_cfg_init.argtypes = [ctypes.POINTER(shot_server_cfg)]
 _lib.shot_server_cfg_init.restype = None
 _lib.shot_server_create.argtypes = [ctypes.POINTER(shot_server_cfg), ctypes.POINTER(_P)]
 _lib.shot_submit.argtypes = [_P, ctypes.POINTER(stencil_desc), _I, _P, ctypes.POINTER(ctypes.c_uint64)]
+_lib.shot_rtm_cfg_init.argtypes = [ctypes.POINTER(shot_rtm_cfg)]
+_lib.shot_rtm_cfg_init.restype = None
+_lib.shot_submit_rtm.argtypes = [_P, ctypes.POINTER(stencil_desc), _I, ctypes.POINTER(shot_rtm_cfg), _P, _P,
+                                 ctypes.POINTER(ctypes.c_uint64)]
 _lib.shot_poll.argtypes = [_P, ctypes.c_uint64, ctypes.POINTER(_I), ctypes.POINTER(shot_timing)]
 _lib.shot_wait.argtypes = [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(_I)]
 _lib.shot_server_get_stats.argtypes = [_P, ctypes.POINTER(shot_server_stats)]
@@ -188,8 +197,8 @@ for _name in ("stencil_plan", "stencil_destroy", "stencil_step", "stencil_run", 
               "stencil_rel_l2", "stencil_set_velocity", "stencil_candidates_1d", "stencil_select",
               "stencil_select_ob", "stencil_sqdiff_noalloc", "stencil_batch_create", "stencil_batch_run",
               "stencil_batch_sync", "stencil_batch_size", "stencil_batch_plan", "stencil_batch_zchunk",
-              "stencil_batch_destroy", "shot_server_create", "shot_submit", "shot_poll", "shot_wait",
-              "shot_server_get_stats", "shot_server_destroy"):
+              "stencil_batch_destroy", "shot_server_create", "shot_submit", "shot_submit_rtm", "shot_poll",
+              "shot_wait", "shot_server_get_stats", "shot_server_destroy"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 
@@ -500,6 +509,32 @@ def shot_submit(server: int, desc: stencil_desc, nsteps: int, out_host=None) -> 
     return t.value
 
 
+def shot_rtm_cfg_init() -> shot_rtm_cfg:
+    """A migration request's defaults: every row of the receiver plane, a
+    snapshot every 10 steps, image scale 1."""
+    c = shot_rtm_cfg()
+    _lib.shot_rtm_cfg_init(ctypes.byref(c))
+    return c
+
+
+def shot_submit_rtm(server: int, desc: stencil_desc, nsteps: int, receiver_z: int, snap_every: int,
+                    image_host, traces_host=None, receiver_y: int = -1, image_scale: float = 1.0) -> int:
+    """Queue a served migration (nsteps forward + nsteps backward steps).
+    image_host: numpy float32 (nz, ny, nx); traces_host: numpy float32
+    (nsteps, ny or 1, nx) or None; both must stay alive until it finishes."""
+    c = shot_rtm_cfg_init()
+    c.receiver_z, c.receiver_y, c.snap_every, c.image_scale = int(receiver_z), int(receiver_y), int(snap_every), \
+        float(image_scale)
+    t = ctypes.c_uint64()
+    ia, idev = _ptr(image_host)
+    ta, tdev = _ptr(traces_host)
+    if idev or tdev or not ia:
+        raise ValueError("image_host (required) and traces_host must be host memory")
+    _check(_lib.shot_submit_rtm(server, ctypes.byref(desc), nsteps, ctypes.byref(c), ia, ta or None,
+                                ctypes.byref(t)))
+    return t.value
+
+
 def shot_poll(server: int, ticket: int) -> tuple[int, shot_timing]:
     st_ = _I()
     tm = shot_timing()
@@ -584,7 +619,7 @@ EXPORTED = [
     "stencil_candidates_1d", "stencil_select", "stencil_select_ob", "stencil_sqdiff_noalloc",
     "stencil_tile_info", "stencil_batch_create", "stencil_batch_run", "stencil_batch_sync",
     "stencil_batch_size", "stencil_batch_plan", "stencil_batch_zchunk", "stencil_batch_destroy",
-    "shot_server_cfg_init", "shot_server_create", "shot_submit", "shot_poll", "shot_wait",
-    "shot_server_get_stats", "shot_server_destroy",
+    "shot_server_cfg_init", "shot_server_create", "shot_submit", "shot_rtm_cfg_init", "shot_submit_rtm",
+    "shot_poll", "shot_wait", "shot_server_get_stats", "shot_server_destroy",
     "stencil_version",
 ]

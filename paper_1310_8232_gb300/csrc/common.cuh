@@ -126,6 +126,20 @@ __device__ __forceinline__ void absorb4(int W, const float2 *tab, int nx, int ny
     }
 }
 
+// The per-step work of a migration served in a group (reverse-time
+// migration around the sweep: record and snapshots going forward, reversed
+// injection and the imaging condition going back), done after each grouped
+// sweep by group_rtm_kernel.  Each phase counts its steps from 0.
+struct GroupRtm {
+    int32_t phase;          // 0 none, 1 forward, 2 backward
+    int32_t z, y;           // receiver plane and row (y < 0: every row)
+    int32_t T, k;           // steps of each phase, snapshot interval (T a multiple of k)
+    float image_scale;
+    float *traces;          // [T][rows][nx]: recorded forward, injected reversed backward
+    float *snaps;           // [T / k][nz][ny][nx]: u at forward times k, 2k, ..., T
+    float *image;           // [nz][ny][nx]
+};
+
 // A shot of a grouped launch: its tensor maps (by parity of the level),
 // buffers and parameters, in 64-byte aligned device memory.
 struct alignas(64) GroupShot {
@@ -137,6 +151,7 @@ struct alignas(64) GroupShot {
     int64_t n_end;                 // step counter value at which the shot stops
     int32_t parity_base;           // buffer of u^n = (n + parity_base) & 1
     int32_t pad;
+    GroupRtm rtm;                  // a served migration's per-step work (phase 0: none)
 };
 struct GroupItem {
     int32_t shot, bx, by, z0, z1;

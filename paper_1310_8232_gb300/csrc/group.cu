@@ -14,8 +14,10 @@ void Group::release()
     graph = nullptr;
     if (d_shots) cudaFree(d_shots);
     if (d_items) cudaFree(d_items);
+    if (d_rtm) cudaFree(d_rtm);
     d_shots = nullptr;
     d_items = nullptr;
+    d_rtm = nullptr;
     cap_shots = cap_items = 0;
 }
 
@@ -71,6 +73,7 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
     absorb = false;
     for (const Plan *p : plans) absorb = absorb || p->absorb_folded();
     h_items.clear();
+    h_rtm.clear();
     int maxnz = 0;
     for (int i = 0; i < n_shots; ++i) {
         const Plan *p = plans[i];
@@ -91,6 +94,8 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
         g.buf[1] = p->buf[1];
         g.n_end = n_end[i];
         g.parity_base = (int)(((p->cur - p->steps_done) % 2 + 2) % 2);
+        g.rtm = p->rtm;
+        if (p->rtm.phase != 0) h_rtm.push_back(i);
         maxnz = std::max(maxnz, p->nz);
     }
     for (int z0 = 0; z0 < maxnz; z0 += zchunk)           // chunk-major over all shots
@@ -106,13 +111,17 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
     cudaError_t e;
     if (n_shots > cap_shots) {
         if (d_shots) cudaFree(d_shots);
+        if (d_rtm) cudaFree(d_rtm);
         d_shots = nullptr;
+        d_rtm = nullptr;
         cap_shots = std::max(n_shots, 2 * cap_shots);
-        if ((e = cudaMalloc(&d_shots, sizeof(GroupShot) * cap_shots)) != cudaSuccess) {
+        if ((e = cudaMalloc(&d_shots, sizeof(GroupShot) * cap_shots)) != cudaSuccess ||
+            (e = cudaMalloc(&d_rtm, sizeof(int) * cap_shots)) != cudaSuccess) {
             cap_shots = 0;
             return fail_cuda(e, "cudaMalloc(group shots)");
         }
     }
+    n_rtm = (int)h_rtm.size();
     if (n_items > cap_items) {
         if (d_items) cudaFree(d_items);
         d_items = nullptr;
@@ -130,6 +139,10 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
         (e = cudaMemcpyAsync(d_items, h_items.data(), sizeof(GroupItem) * n_items, cudaMemcpyHostToDevice,
                              stream)) != cudaSuccess)
         return fail_cuda(e, "group items upload");
+    if (n_rtm &&
+        (e = cudaMemcpyAsync(d_rtm, h_rtm.data(), sizeof(int) * n_rtm, cudaMemcpyHostToDevice, stream)) !=
+            cudaSuccess)
+        return fail_cuda(e, "group migration list upload");
     // the host vectors must outlive the copies
     if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail_cuda(e, "group upload");
     return STENCIL_OK;
@@ -143,6 +156,7 @@ int Group::step(int k)
     auto enqueue = [&](int steps) -> cudaError_t {
         for (int i = 0; i < steps; ++i) {
             cudaError_t r = launch_grouped(R, storage, tx, ty, d_shots, d_items, n_items, i, absorb, stream);
+            if (r == cudaSuccess && n_rtm) r = launch_group_rtm(d_shots, d_rtm, n_rtm, i, stream);
             if (r != cudaSuccess) return r;
         }
         return launch_group_advance(d_shots, n_shots, steps, stream);

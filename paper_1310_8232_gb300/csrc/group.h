@@ -14,10 +14,12 @@ struct Group {
     cudaStream_t stream = nullptr;
     GroupShot *d_shots = nullptr;
     GroupItem *d_items = nullptr;
+    int *d_rtm = nullptr;           // indices of the shots with migration work (GroupRtm)
     int cap_shots = 0, cap_items = 0;
-    int n_shots = 0, n_items = 0;
+    int n_shots = 0, n_items = 0, n_rtm = 0;
     std::vector<GroupShot> h_shots;
     std::vector<GroupItem> h_items;
+    std::vector<int> h_rtm;
     int graph_len = 0;
     cudaGraphExec_t graph = nullptr;
 

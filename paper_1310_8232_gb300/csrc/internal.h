@@ -125,6 +125,8 @@ cudaError_t launch_grouped_bf16(int R, int tx, int ty, const GroupShot *shots, c
                                 int step_off, bool absorb, cudaStream_t s);
 // n[i] = min(n[i] + k, n_end[i]) for the shots of a group
 cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStream_t s);
+// the served migrations' per-step work (GroupRtm) of the shots shots[list[i]]
+cudaError_t launch_group_rtm(const GroupShot *shots, const int *list, int n_list, int step_off, cudaStream_t s);
 
 // ---- K2 helpers: 16-bit fields <-> FP32 with per-plane power-of-two scales ----
 // pack: v = src (or src - sub when sub is not null), FP32 (pitch elements)

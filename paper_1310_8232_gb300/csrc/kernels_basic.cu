@@ -293,6 +293,64 @@ cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStrea
     return cudaGetLastError();
 }
 
+// The per-step work of served migrations (GroupRtm), after the grouped sweep
+// of step n = *step_base + step_off; blockIdx.y picks the shot from `list`.
+// On most steps only the receiver rows are touched (record going forward,
+// injection of the reversed traces going back); on the steps whose field is
+// a snapshot time the blocks sweep the whole field, each thread doing the
+// receiver-row work of its point first, then the snapshot copy (forward) or
+// the imaging condition (backward).  The arithmetic is that of the single
+// plan's record, injection and imaging kernels: a copy, u += 1 * trace, and
+// img = fmaf(scale * s, u, img).
+__global__ void group_rtm_kernel(const GroupShot *shots, const int *list, int step_off)
+{
+    const GroupShot &g = shots[list[blockIdx.y]];
+    const int64_t n = *g.prm.step_base + step_off;
+    if (n >= g.n_end) return;                           // uniform over the block
+    const GroupRtm o = g.rtm;
+    const int nx = g.prm.nx, ny = g.prm.ny, nz = g.prm.nz;
+    const int64_t pitch = g.prm.pitch, plane = g.prm.plane;
+    float *u = static_cast<float *>(g.buf[(int)((n + 1 + g.parity_base) & 1)]);   // u^{n+1}
+    const int rows = o.y < 0 ? ny : 1;
+    const int64_t per = (int64_t)rows * nx;             // elements of one trace step
+    const bool fwd = o.phase == 1;
+    const int64_t tb = o.T - n;                         // backward: forward time of the field after this step
+    const bool field = fwd ? (n + 1) % o.k == 0 : (tb % o.k == 0 && tb >= o.k);
+    const float inj_scale = 1.0f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (!field) {
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per; t += stride) {
+            const int r = (int)(t / nx), x = (int)(t - (int64_t)r * nx);
+            const int64_t q = o.z * plane + (int64_t)(o.y < 0 ? r : o.y) * pitch + x;
+            if (fwd) o.traces[n * per + t] = u[q];
+            else u[q] += inj_scale * o.traces[(o.T - 1 - n) * per + t];
+        }
+        return;
+    }
+    const int64_t pts = (int64_t)nx * ny * nz, sl = fwd ? (n + 1) / o.k - 1 : tb / o.k - 1;
+    float *snap = o.snaps + sl * pts;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pts; i += stride) {
+        const int64_t row = i / nx;
+        const int x = (int)(i - row * nx);
+        const int z = (int)(row / ny), y = (int)(row - (int64_t)z * ny);
+        const int64_t q = row * pitch + x;
+        if (z == o.z && (o.y < 0 || y == o.y)) {
+            const int64_t t = (int64_t)(o.y < 0 ? y : 0) * nx + x;
+            if (fwd) o.traces[n * per + t] = u[q];
+            else u[q] += inj_scale * o.traces[(o.T - 1 - n) * per + t];
+        }
+        if (fwd) snap[i] = u[q];
+        else o.image[i] = fmaf(o.image_scale * snap[i], u[q], o.image[i]);
+    }
+}
+
+cudaError_t launch_group_rtm(const GroupShot *shots, const int *list, int n_list, int step_off, cudaStream_t s)
+{
+    if (n_list <= 0) return cudaSuccess;
+    group_rtm_kernel<<<dim3(152 * 8, n_list), 256, 0, s>>>(shots, list, step_off);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s)
 {
     advance_kernel<<<1, 1, 0, s>>>(n, k);

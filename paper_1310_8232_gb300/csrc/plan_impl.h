@@ -126,6 +126,8 @@ struct Plan {
     int inj_steps = 0, inj_reverse = 0, inj_z = -1, inj_y = -1;
     float inj_scale = 0.0f;
     // tile selection results
+    // a served migration's per-step work in grouped launches (phase 0: none)
+    GroupRtm rtm{};
     int tune_mode = 0;
     double min_time_ms = NAN, actual_time_ms = NAN, full_time_ms = NAN, quality = NAN, selection_ms = NAN;
     int n_candidates = 0;

@@ -52,7 +52,21 @@ struct Request {
     int64_t steps_done = 0;
     int64_t bytes = 0;
     Plan *plan = nullptr;
+    // a served migration (shot_submit_rtm): phase 0 forward, 1 backward
+    bool rtm = false;
+    shot_rtm_cfg rtm_cfg{};
+    float *image_host = nullptr, *traces_host = nullptr;
+    int phase = 0;
+    float *d_rtm = nullptr;           // traces | snapshots | image, one pool allocation
 };
+
+// Device bytes of a migration's traces, snapshots and image (dense FP32).
+int64_t rtm_bytes(const stencil_desc &d, int32_t nsteps, const shot_rtm_cfg &c)
+{
+    const int64_t pts = (int64_t)d.nx * d.ny * d.nz;
+    const int64_t rows = c.receiver_y < 0 ? d.ny : 1;
+    return 4 * ((int64_t)nsteps * rows * d.nx + (int64_t)(nsteps / c.snap_every) * pts + pts);
+}
 
 int64_t projected_bytes(const stencil_desc &d)
 {
@@ -254,6 +268,23 @@ void Server::finish(Request *r, int status)
         r->plan->stream = retire_stream;
         r->plan->own_stream = false;
         if (rc == STENCIL_OK && r->out_host) rc = read_back(r->plan, r->out_host);
+        if (r->d_rtm) {
+            // a migration: the image (and the traces) are dense on the device
+            const stencil_desc &d = r->desc;
+            const int64_t pts = (int64_t)d.nx * d.ny * d.nz;
+            const int64_t tr = (int64_t)r->nsteps * (r->rtm_cfg.receiver_y < 0 ? d.ny : 1) * d.nx;
+            const float *image = r->d_rtm + tr + (int64_t)(r->nsteps / r->rtm_cfg.snap_every) * pts;
+            cudaError_t e = cudaSuccess;
+            if (rc == STENCIL_OK && r->image_host)
+                e = cudaMemcpyAsync(r->image_host, image, sizeof(float) * pts, cudaMemcpyDeviceToHost, retire_stream);
+            if (rc == STENCIL_OK && e == cudaSuccess && r->traces_host)
+                e = cudaMemcpyAsync(r->traces_host, r->d_rtm, sizeof(float) * tr, cudaMemcpyDeviceToHost,
+                                    retire_stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(retire_stream);
+            if (e != cudaSuccess && rc == STENCIL_OK) rc = fail_cuda(e, "migration read-back");
+            cudaFreeAsync(r->d_rtm, retire_stream);
+            r->d_rtm = nullptr;
+        }
         r->plan->release();
         delete r->plan;
         r->plan = nullptr;
@@ -267,7 +298,7 @@ void Server::finish(Request *r, int status)
     stats.running -= 1;
     if (rc == STENCIL_OK) {
         stats.done += 1;
-        stats.point_updates += (int64_t)r->desc.nx * r->desc.ny * r->desc.nz * r->nsteps;
+        stats.point_updates += (int64_t)r->desc.nx * r->desc.ny * r->desc.nz * r->nsteps * (r->rtm ? 2 : 1);
     } else {
         stats.failed += 1;
     }
@@ -336,10 +367,29 @@ void Server::end_chunk(Lane &L, int rc)
         p->cur = (int)((p->steps_done + pb) & 1);
         {
             std::lock_guard<std::mutex> lock(mu);
-            r->steps_done = p->steps_done;
+            r->steps_done = (int64_t)r->phase * r->nsteps + p->steps_done;
         }
         if (rc != STENCIL_OK) {
             retire(r, rc);
+            L.rebuild = true;
+        } else if (p->steps_done >= r->nsteps && r->rtm && r->phase == 0) {
+            // a migration's forward phase is done: the same plan goes back
+            // in time from zero fields without its point source (no chunk of
+            // this lane is in flight behind this one, see run())
+            const size_t fbytes = (size_t)p->field_elems * p->esize;
+            cudaError_t e = cudaMemsetAsync(p->buf[0], 0, fbytes, L.stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->buf[1], 0, fbytes, L.stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(p->d_step, 0, sizeof(int64_t), L.stream);
+            if (e != cudaSuccess) {
+                retire(r, fail_cuda(e, "migration backward set-up"));
+            } else {
+                r->phase = 1;
+                p->src.on = 0;
+                p->rtm.phase = 2;
+                p->steps_done = 0;
+                p->cur = 0;
+                keep.push_back(r);
+            }
             L.rebuild = true;
         } else if (p->steps_done >= r->nsteps) {
             retire(r, p->check_device_error());
@@ -448,6 +498,33 @@ void Server::run()
             if (arc) {
                 retire(r, arc);
                 continue;
+            }
+            if (r->rtm) {
+                // the migration's traces, snapshots and image (zeroed), from the pool
+                const stencil_desc &dd = r->desc;
+                const int64_t pts = (int64_t)dd.nx * dd.ny * dd.nz;
+                const int64_t tr = (int64_t)r->nsteps * (r->rtm_cfg.receiver_y < 0 ? dd.ny : 1) * dd.nx;
+                const int64_t ns = r->nsteps / r->rtm_cfg.snap_every;
+                cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&r->d_rtm),
+                                                        rtm_bytes(dd, r->nsteps, r->rtm_cfg), pool, admit_stream);
+                if (e == cudaSuccess)
+                    e = cudaMemsetAsync(r->d_rtm + tr + ns * pts, 0, sizeof(float) * pts, admit_stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(admit_stream);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    r->plan = p;
+                    retire(r, fail(STENCIL_ENOMEM, "migration buffers: %s", cudaGetErrorString(e)));
+                    continue;
+                }
+                p->rtm.phase = 1;
+                p->rtm.z = r->rtm_cfg.receiver_z;
+                p->rtm.y = r->rtm_cfg.receiver_y;
+                p->rtm.T = r->nsteps;
+                p->rtm.k = r->rtm_cfg.snap_every;
+                p->rtm.image_scale = r->rtm_cfg.image_scale;
+                p->rtm.traces = r->d_rtm;
+                p->rtm.snaps = r->d_rtm + tr;
+                p->rtm.image = r->d_rtm + tr + ns * pts;
             }
             Lane &L = *lanes[lane_of(r->desc, (int)lanes.size())];
             p->stream = L.stream;               // the lane's stream from here on
@@ -598,7 +675,39 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
     return STENCIL_OK;
 }
 
+static int submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float *out_host, const shot_rtm_cfg *rtm,
+                  float *image_host, float *traces_host, uint64_t *ticket);
+
 int shot_submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float *out_host, uint64_t *ticket)
+{
+    return submit(h, d, nsteps, out_host, nullptr, nullptr, nullptr, ticket);
+}
+
+void shot_rtm_cfg_init(shot_rtm_cfg *c)
+{
+    if (!c) return;
+    std::memset(c, 0, sizeof *c);
+    c->receiver_y = -1;
+    c->snap_every = 10;
+    c->image_scale = 1.0f;
+}
+
+int shot_submit_rtm(shot_server_t h, const stencil_desc *d, int32_t nsteps, const shot_rtm_cfg *cfg,
+                    float *image_host, float *traces_host, uint64_t *ticket)
+{
+    if (!h || !d || !cfg || !image_host || !ticket) return fail(STENCIL_EINVAL, "null argument");
+    Server *s = reinterpret_cast<Server *>(h);
+    if (s->cfg.storage != STENCIL_FP32) return fail(STENCIL_EUNSUPPORTED, "migrations need an FP32 server");
+    if (nsteps < 1 || cfg->snap_every < 1 || nsteps % cfg->snap_every)
+        return fail(STENCIL_EINVAL, "nsteps must be a positive multiple of snap_every");
+    if (cfg->receiver_z < 0 || cfg->receiver_z >= d->nz || cfg->receiver_y < -1 || cfg->receiver_y >= d->ny)
+        return fail(STENCIL_EINVAL, "receiver outside the grid");
+    if (!std::isfinite(cfg->image_scale)) return fail(STENCIL_EINVAL, "image_scale must be finite");
+    return submit(h, d, nsteps, nullptr, cfg, image_host, traces_host, ticket);
+}
+
+static int submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float *out_host, const shot_rtm_cfg *rtm,
+                  float *image_host, float *traces_host, uint64_t *ticket)
 {
     if (!h || !d || !ticket) return fail(STENCIL_EINVAL, "null argument");
     if (nsteps < 0) return fail(STENCIL_EINVAL, "nsteps < 0");
@@ -615,6 +724,13 @@ int shot_submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float *o
     r->nsteps = nsteps;
     r->out_host = out_host;
     r->bytes = projected_bytes(r->desc);
+    if (rtm) {
+        r->rtm = true;
+        r->rtm_cfg = *rtm;
+        r->image_host = image_host;
+        r->traces_host = traces_host;
+        r->bytes += rtm_bytes(r->desc, nsteps, *rtm);
+    }
     if (!d->velocity_on_device) {
         // the request keeps its own copy of the model until admission
         const size_t n = (size_t)d->nx * d->ny * d->nz;

@@ -198,6 +198,11 @@ static void layout(void)
     OF(shot_server_cfg, tile);
     OF(shot_server_cfg, lanes);
     OF(shot_server_cfg, pad);
+    SZ(shot_rtm_cfg);
+    OF(shot_rtm_cfg, receiver_z);
+    OF(shot_rtm_cfg, receiver_y);
+    OF(shot_rtm_cfg, snap_every);
+    OF(shot_rtm_cfg, image_scale);
     SZ(shot_timing);
     OF(shot_timing, t_submit);
     OF(shot_timing, t_admit);

@@ -285,3 +285,68 @@ def test_batch_and_server_with_absorbing_layers_equal_alone(env):
         st.shot_server_destroy(server)
     for ((v, dt, src), a), (t, out) in zip(zip(shots, layers), jobs):
         assert np.array_equal(out, alone(env, v, dt, src, 23, absorb=a))
+
+
+def test_served_migrations_equal_single_plan_migrations(env):
+    """Reverse-time migrations through the shot server (forward with record
+    and snapshots, then backward with the reversed traces injected and the
+    imaging condition, in the lanes beside ordinary shots; snapshots fall in
+    the middle of the lane's chunks): image and traces bit-identical to the
+    single-plan migration (rtm.migrate) with the server's tile, and the
+    ordinary shots to their alone runs."""
+    torch, st = env
+    from paper_1310_8232_gb300 import rtm
+    jobs = [((48, 40, 36), 36, 6, 4, (6, 0.2)), ((56, 30, 44), 30, 5, 7, (0, 0.0)),
+            ((70, 66, 40), 24, 4, 3, (5, 0.25))]
+    server = make_server(st, chunk_steps=5)
+    subs, plain = [], []
+    try:
+        for i, (shape, T, k, zr, ab) in enumerate(jobs):
+            v, dt, src = shot(60 + i, shape)
+            img = np.full_like(v, np.nan)
+            tr = np.full((T, shape[1], shape[0]), np.nan, dtype=np.float32)
+            t = st.shot_submit_rtm(server, st.make_desc(v, dt, radius=5, src=src, absorb=ab), T, zr, k, img, tr)
+            subs.append((t, v, dt, src, T, k, zr, ab, img, tr))
+            if i == 1:                                     # ordinary shots arriving in between
+                for j, s in enumerate(SHAPES[:2]):
+                    pv, pdt, psrc = shot(70 + j, s)
+                    out = np.full_like(pv, np.nan)
+                    plain.append((st.shot_submit(server, st.make_desc(pv, pdt, radius=5, src=psrc), 17, out),
+                                  pv, pdt, psrc, out))
+        for t, *_ in subs + plain:
+            assert st.shot_wait(server, t, 120.0) == st.SHOT_DONE
+        state, tm = st.shot_poll(server, subs[0][0])
+        assert tm.steps_done == 2 * jobs[0][1]
+    finally:
+        st.shot_server_destroy(server)
+    for t, v, dt, src, T, k, zr, ab, img, tr in subs:
+        want_img, want_tr = rtm.migrate(torch, torch.from_numpy(v).cuda(), dt, T, src, zr, k, radius=5,
+                                        dx=workloads.DX, absorb=ab, tile=(2, 64, 16, -1))
+        assert np.array_equal(tr, want_tr.cpu().numpy())
+        assert np.array_equal(img, want_img.cpu().numpy())
+        assert np.any(img != 0)
+    for t, pv, pdt, psrc, out in plain:
+        assert np.array_equal(out, alone(env, pv, pdt, psrc, 17))
+
+
+def test_served_migration_refusals(env):
+    torch, st = env
+    v, dt, src = shot(80, (40, 40, 40))
+    img = np.zeros_like(v)
+    server = make_server(st)
+    try:
+        for T, k, zr in ((30, 7, 4), (0, 5, 4), (30, 5, 40), (30, 0, 4)):
+            with pytest.raises(st.StencilError) as ei:
+                st.shot_submit_rtm(server, st.make_desc(v, dt, radius=5, src=src), T, zr, k, img)
+            assert ei.value.code == st.STENCIL_EINVAL
+    finally:
+        st.shot_server_destroy(server)
+    cfg = st.shot_server_cfg_init()
+    cfg.storage = 1
+    half = st.shot_server_create(cfg)
+    try:
+        with pytest.raises(st.StencilError) as ei:
+            st.shot_submit_rtm(half, st.make_desc(v, dt, radius=5, src=src), 30, 4, 5, img)
+        assert ei.value.code == st.STENCIL_EUNSUPPORTED
+    finally:
+        st.shot_server_destroy(half)

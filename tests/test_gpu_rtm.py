@@ -145,8 +145,10 @@ def test_one_shot_migration_matches_oracle(env, k):
     image, traces = rtm.migrate(torch, torch.from_numpy(v).cuda(), dt, T, src, zr, snap, radius=R, dx=DX,
                                 absorb=absorb, f=25.0, tile=tiles(st)[k], graph_steps=6)
     ref_img, ref_tr, _ = oracle_rtm.migrate(v, DX, dt, R, T, src, zr, snap, absorb=absorb, f=25.0)
-    check(traces.cpu().numpy(), ref_tr, 2e-5)
-    check(image.cpu().numpy(), ref_img, 1e-4)
+    # the FP32 bar for both: measured 1.4e-6 (traces) and 4.6e-7 (image)
+    e_tr = check(traces.cpu().numpy(), ref_tr, TOL)
+    e_img = check(image.cpu().numpy(), ref_img, TOL)
+    print(f"\nmigration vs FP64 oracle: traces {e_tr:.3e}, image {e_img:.3e}")
 
 
 def test_unsupported_combinations_are_refused(env):
