@@ -429,8 +429,9 @@ STENCIL_API int shot_server_create(const shot_server_cfg *cfg, shot_server_t *ou
  * nx*ny*nz floats, or NULL), which must stay valid until the shot is DONE or
  * FAILED.  A page-locked out_host (cudaHostAlloc, cudaHostRegister) is
  * written by one device-to-host copy, any other through the server's pinned
- * bounce buffers.  A host velocity is copied at once; a device velocity must stay
- * valid until the shot is admitted.  STENCIL_EBUDGET if the shot alone
+ * bounce buffers.  A pageable host velocity is copied at once; a page-locked
+ * host velocity or a device velocity is read in place at admission and must
+ * stay valid until the shot is RUNNING (or DONE / FAILED).  STENCIL_EBUDGET if the shot alone
  * exceeds the budget (it is recorded as FAILED). */
 STENCIL_API int shot_submit(shot_server_t s, const stencil_desc *d, int32_t nsteps, float *out_host,
                             uint64_t *ticket);

@@ -732,10 +732,17 @@ static int submit(shot_server_t h, const stencil_desc *d, int32_t nsteps, float 
         r->bytes += rtm_bytes(r->desc, nsteps, *rtm);
     }
     if (!d->velocity_on_device) {
-        // the request keeps its own copy of the model until admission
-        const size_t n = (size_t)d->nx * d->ny * d->nz;
-        r->velocity.assign(d->velocity, d->velocity + n);
-        r->desc.velocity = r->velocity.data();
+        // a page-locked model is read in place at admission (one direct
+        // copy); any other is copied now, so the caller may free it at once
+        cudaPointerAttributes attr{};
+        const bool pinned = cudaPointerGetAttributes(&attr, d->velocity) == cudaSuccess &&
+                            attr.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        if (!pinned) {
+            const size_t n = (size_t)d->nx * d->ny * d->nz;
+            r->velocity.assign(d->velocity, d->velocity + n);
+            r->desc.velocity = r->velocity.data();
+        }
     }
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stopping) return fail(STENCIL_ECANCELLED, "the server is shutting down");

@@ -350,3 +350,19 @@ def test_served_migration_refusals(env):
         assert ei.value.code == st.STENCIL_EUNSUPPORTED
     finally:
         st.shot_server_destroy(half)
+
+
+def test_server_reads_a_page_locked_model_in_place(env):
+    """A page-locked host velocity is read at admission (not copied at
+    submit): the result is the shot's alone run."""
+    torch, st = env
+    v, dt, src = shot(90, (67, 45, 33))
+    pinned = torch.from_numpy(v).pin_memory()
+    server = make_server(st)
+    out = np.full_like(v, np.nan)
+    try:
+        t = st.shot_submit(server, st.make_desc(pinned, dt, radius=5, src=src), 19, out)
+        assert st.shot_wait(server, t, 60.0) == st.SHOT_DONE
+    finally:
+        st.shot_server_destroy(server)
+    assert np.array_equal(out, alone(env, v, dt, src, 19))
