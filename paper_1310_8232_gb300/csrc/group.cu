@@ -8,13 +8,25 @@
 
 namespace stencil {
 
+cudaError_t Group::alloc(void **p, size_t bytes)
+{
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, stream) : cudaMalloc(p, bytes);
+}
+
+void Group::free_dev(void *p)
+{
+    if (!p) return;
+    if (pool) cudaFreeAsync(p, stream);
+    else cudaFree(p);
+}
+
 void Group::release()
 {
     if (graph) cudaGraphExecDestroy(graph);
     graph = nullptr;
-    if (d_shots) cudaFree(d_shots);
-    if (d_items) cudaFree(d_items);
-    if (d_rtm) cudaFree(d_rtm);
+    free_dev(d_shots);
+    free_dev(d_items);
+    free_dev(d_rtm);
     d_shots = nullptr;
     d_items = nullptr;
     d_rtm = nullptr;
@@ -110,23 +122,23 @@ int Group::build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n
     n_items = (int)h_items.size();
     cudaError_t e;
     if (n_shots > cap_shots) {
-        if (d_shots) cudaFree(d_shots);
-        if (d_rtm) cudaFree(d_rtm);
+        free_dev(d_shots);
+        free_dev(d_rtm);
         d_shots = nullptr;
         d_rtm = nullptr;
         cap_shots = std::max(n_shots, 2 * cap_shots);
-        if ((e = cudaMalloc(&d_shots, sizeof(GroupShot) * cap_shots)) != cudaSuccess ||
-            (e = cudaMalloc(&d_rtm, sizeof(int) * cap_shots)) != cudaSuccess) {
+        if ((e = alloc(reinterpret_cast<void **>(&d_shots), sizeof(GroupShot) * cap_shots)) != cudaSuccess ||
+            (e = alloc(reinterpret_cast<void **>(&d_rtm), sizeof(int) * cap_shots)) != cudaSuccess) {
             cap_shots = 0;
             return fail_cuda(e, "cudaMalloc(group shots)");
         }
     }
     n_rtm = (int)h_rtm.size();
     if (n_items > cap_items) {
-        if (d_items) cudaFree(d_items);
+        free_dev(d_items);
         d_items = nullptr;
         cap_items = std::max(n_items, 2 * cap_items);
-        if ((e = cudaMalloc(&d_items, sizeof(GroupItem) * cap_items)) != cudaSuccess) {
+        if ((e = alloc(reinterpret_cast<void **>(&d_items), sizeof(GroupItem) * cap_items)) != cudaSuccess) {
             cap_items = 0;
             return fail_cuda(e, "cudaMalloc(group items)");
         }

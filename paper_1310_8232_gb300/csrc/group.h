@@ -12,6 +12,9 @@ struct Group {
     int R = 5, storage = 0, tx = 64, ty = 16, zchunk = 32;
     bool absorb = false;            // some shot has an absorbing layer: the absorbing variant
     cudaStream_t stream = nullptr;
+    // set: the device tables come from this stream-ordered pool on `stream`
+    // (no device-wide synchronisation when they grow, as cudaFree would do)
+    cudaMemPool_t pool = nullptr;
     GroupShot *d_shots = nullptr;
     GroupItem *d_items = nullptr;
     int *d_rtm = nullptr;           // indices of the shots with migration work (GroupRtm)
@@ -25,6 +28,8 @@ struct Group {
 
     ~Group() { release(); }
     void release();
+    cudaError_t alloc(void **p, size_t bytes);
+    void free_dev(void *p);
     // Describe `plans` (same radius, storage and tile shape) to the device;
     // shot i stops when its counter reaches n_end[i].  Enqueued on stream.
     int build(const std::vector<Plan *> &plans, const std::vector<int64_t> &n_end);

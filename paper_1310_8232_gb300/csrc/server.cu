@@ -666,6 +666,7 @@ int shot_server_create(const shot_server_cfg *cfg, shot_server_t *out)
             return fail_cuda(e, "pinned read-back buffers");
     uint64_t keep = (uint64_t)s->budget;                 // keep freed memory for the next shots
     cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    for (auto &L : s->lanes) L->group.pool = s->pool;    // group tables without device-wide syncs
     s->stats.budget_bytes = s->budget;
     s->t0 = Clock::now();
     Server *raw = s.get();
