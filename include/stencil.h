@@ -219,12 +219,14 @@ STENCIL_API int stencil_sync(stencil_plan_t p);
 
 /* ---- state ------------------------------------------------------------ */
 
-/* Copy u^n (which = 0) or u^{n-1} (which = 1) out as a dense FP32 array.
+/* Copy u^n (which = 0) or u^{n-1} (which = 1) out as a dense FP32 array
+ * (16-bit storage: u^{n-1} = u^n - d^n from the two stored fields).
  * Synchronous. */
 STENCIL_API int stencil_get_field(stencil_plan_t p, int32_t which, float *out, int32_t out_on_device);
 
 /* Set the state: u^n = u, u^{n-1} = u_prev (dense FP32; NULL = zeros), and
- * the step counter n = step.  Synchronous. */
+ * the step counter n = step (16-bit storage keeps u^n and d^n = u^n -
+ * u^{n-1}, each rounded once with its plane's scale).  Synchronous. */
 STENCIL_API int stencil_set_fields(stencil_plan_t p, const float *u, const float *u_prev,
                        int32_t on_device, int64_t step);
 
@@ -314,20 +316,21 @@ STENCIL_API int stencil_image_accumulate(stencil_plan_t p, const float *snapshot
  * first copy of every block is expected to bring 16 more bytes than it
  * does, so that block's first wait runs out after wait_ns nanoseconds (0 =
  * the default 2 s).  enable = 0 restores normal sweeps (wait_ns stays the
- * wait limit).  Tiled kernel only (STENCIL_EUNSUPPORTED otherwise).  The
- * paper has no counterpart; for tests of the error path. */
+ * wait limit).  Tiled and two-step kernels only (STENCIL_EUNSUPPORTED
+ * otherwise).  The paper has no counterpart; for tests of the error path. */
 STENCIL_API int stencil_debug_wait_fault(stencil_plan_t p, int32_t enable, uint32_t wait_ns);
 
 /* ---- checkpoint / restore ---------------------------------------------
  * The time loop's state (Sec. 2, Algorithm 1): the two levels u^n and
- * u^{n-1} in the plan's storage encoding, the step n (the source reads
- * w(n dt)) and, for 16-bit storage, the per-plane scales and maxima of those
- * two levels.  A plan restored from a checkpoint continues bit for bit as
- * the plan that wrote it would have.  Format: a 128-byte header (magic
- * "STNCKPT1", version 1, dims, radius, storage, element size, step, dx, dt,
- * source position / frequency / delay / scale, payload bytes), then u^n and
- * u^{n-1} dense (x fastest), then for 16-bit storage scale[n], scale[n-1]
- * (nz floats each) and max[n], max[n-1] (nz uint32 each).  The velocity
+ * u^{n-1} (16-bit storage: u^n and d^n = u^n - u^{n-1}) in the plan's
+ * storage encoding, the step n (the source reads w(n dt)) and, for 16-bit
+ * storage, the per-plane scales and maxima of u^n and d^n.  A plan restored
+ * from a checkpoint continues bit for bit as the plan that wrote it would
+ * have.  Format: a 128-byte header (magic "STNCKPT1", version 2, dims,
+ * radius, storage, element size, step, dx, dt, source position / frequency /
+ * delay / scale, payload bytes), then u^n and u^{n-1} (or d^n) dense (x
+ * fastest), then for 16-bit storage the scales of u^n and d^n (nz floats
+ * each) and their maxima (nz uint32 each).  The velocity
  * model is not included: restore into a plan made from the same descriptor
  * (dims, radius, storage, dx, dt and source are checked, STENCIL_EINVAL on a
  * mismatch; a different velocity model at the source point is caught, one

@@ -8,7 +8,8 @@
 //   * one TMA box of u^n, (TX + 2 HX) x (TY + 2R), lands in a shared-memory
 //     ring of SU stages (out-of-range coordinates are zero-filled by the TMA
 //     unit, which is exactly the ghost-zero Dirichlet boundary);
-//   * TMA boxes of u^{n-1} and kappa (TX x TY) land in a ring of SA stages;
+//   * TMA boxes of u^{n-1} (16-bit storage: d^n, see below) and kappa
+//     (TX x TY) land in a ring of SA stages;
 //   * each thread owns 4 consecutive x points in each of 2 rows (the y
 //     neighbours it loads serve both rows).  When plane p lands, the thread
 //     reads its own values and its x and y neighbours (shared-memory

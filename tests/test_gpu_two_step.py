@@ -237,3 +237,34 @@ def test_refused_combinations(env):
         assert ei.value.code == st.STENCIL_EUNSUPPORTED
     finally:
         st.stencil_destroy(plan)
+
+
+def test_checkpoint_restore_continues_bit_for_bit(env):
+    """A two-step plan checkpointed after an odd count (its levels sit in
+    their pair the other way round) and restored into a fresh two-step plan:
+    both continue with the same launches and agree bit for bit."""
+    torch, st = env
+    n, R = 60, 5
+    v = workloads.layered_velocity(n, n, n, seed=76)
+    dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
+    src = (n // 2, n // 3, n // 2)
+    mk = lambda: st.stencil_plan(st.make_desc(v, dt, radius=R, src=src, tile=two_step(st), stream=stream(torch)))
+    a, b = mk(), mk()
+    try:
+        st.stencil_step(a, 7)
+        ck = st.stencil_checkpoint(a)
+        st.stencil_restore(b, ck)
+        outs = []
+        for plan in (a, b):
+            st.stencil_step(plan, 9)
+            u, up = np.empty_like(v), np.empty_like(v)
+            st.stencil_get_field(plan, 0, u)
+            st.stencil_get_field(plan, 1, up)
+            outs.append((u, up))
+        assert st.stencil_get_stats(b).steps_done == 16
+    finally:
+        st.stencil_destroy(a)
+        st.stencil_destroy(b)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ref, _ = oracle.run(v, workloads.DX, dt, R, 16, src=src)
+    check(outs[0][0], ref)
