@@ -191,10 +191,14 @@ __device__ __forceinline__ void dispatch(int k, F &f)
 }
 
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
-// 1 / max(kappa, FLT_MIN) for two points (the hardware reciprocal; energy sums only)
+// 1 / (kappa + FLT_MIN) for two points (the hardware reciprocal; energy sums
+// only).  The packed add leaves every kappa >= 2^-100 unchanged and keeps
+// the reciprocal finite where kappa is the zero fill outside the grid (there
+// u^{n+1} - u^n = 0, so the term is 0, not NaN).
 __device__ __forceinline__ float2 rcp_kappa2(const float2 &k)
 {
-    return make_float2(rcp_approx(fmaxf(k.x, 1.17549435e-38f)), rcp_approx(fmaxf(k.y, 1.17549435e-38f)));
+    const float2 kk = __fadd2_rn(k, make_float2(1.17549435e-38f, 1.17549435e-38f));
+    return make_float2(rcp_approx(kk.x), rcp_approx(kk.y));
 }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float4 scale4(const float4 &v, float s)
@@ -474,7 +478,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             else if (k == 2) nxt.z += src_add;
                             else nxt.w += src_add;
                         }
-                        if (REC && p.energy_on) {
+                        if (REC) {
                             // E^{n+1/2} terms (u^{n+1} - u^n)^2 / kappa (into ekin) and
                             // u^{n+1} Lambda(u^n) (into epot)
                             const float2 uA = lo2(nxt), uB = hi2(nxt);
@@ -509,7 +513,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                 }
             };
             Unroll<0, S::RING>::run(body);
-            if (REC && p.energy_on) eacc += (double)((ekin.x + ekin.y) - (epot.x + epot.y));
+            if (REC) eacc += (double)((ekin.x + ekin.y) - (epot.x + epot.y));
         }
     } else {
         // The same per-plane work with the ring slot chosen at run time.  The
@@ -644,7 +648,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float2 oB = __fadd2_rn(hi2(cc), hi2(dnx));
                         const float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
                         const bool ok = x_ok && gy0 + h < p.ny;
-                        if (REC && p.energy_on) {
+                        if (REC) {
                             // (u^{n+1} - u^n) = d^{n+1}: its square over kappa, and u^{n+1} Lambda(u^n)
                             const float2 dA = lo2(dnx), dB = hi2(dnx);
                             ekin = __ffma2_rn(__fmul2_rn(dA, dA), rcp_kappa2(lo2(kap)), ekin);
@@ -692,7 +696,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                     wmax[(i & 1) * 2 * (S::NT / 32) + (S::NT / 32) + (tid >> 5)] = wd;
                 }
             }
-            if (REC && p.energy_on && (k == S::RING - 1 || i == nin - 1)) {
+            if (REC && (k == S::RING - 1 || i == nin - 1)) {
                 eacc += (double)((ekin.x + ekin.y) - (epot.x + epot.y));
                 ekin = epot = make_float2(0.f, 0.f);
             }
@@ -720,7 +724,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
             }
         }
     }
-    if (REC && p.energy_on) {
+    if (REC) {
         // the warp's sum of its threads' FP64 energy terms (fixed order)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) eacc += __shfl_xor_sync(0xffffffffu, eacc, off);
@@ -742,7 +746,8 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
 }
 
 // One shot per launch: block (tile, z-chunk) from the grid position.  REC:
-// the variant that also sums the step's energy; ABS: the variant with the
+// the variant that also sums the step's energy (launched only when
+// p.energy_on is set, so the kernel does not test it); ABS: the variant with the
 // absorbing layer folded in (FP32).
 template <int R, int TX, int TY, typename E, bool REC = false, bool ABS = false>
 __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX, TY, E>::MINB)
@@ -756,25 +761,40 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
     const int z1 = min(z0 + p.zchunk, p.nz);
     const int64_t n = current_step(p);
     sweep_tile<R, TX, TY, E, REC, ABS>(&map_u, &map_up, &map_k, p, bx, by, z0, z1, n, smem);
-    if (REC && p.energy_on) {
-        // block partial (warps in order), then the last block to finish adds
-        // all partials in block order: the step's energy, deterministic
+    if constexpr (REC) {
+        // block partial (warps in order); the last block to finish then
+        // adds all partials: thread t the blocks t, t + NT, ... in order,
+        // then a fixed tree over the threads.  The step's energy depends
+        // only on the data, and the tail after the last block's sweep is
+        // ~nblk / NT loads per thread instead of nblk serial ones.
         using S = TiledShape<R, TX, TY, E>;
+        __shared__ double red[S::NT];
+        __shared__ unsigned last;
+        const unsigned nblk = gridDim.x * gridDim.y;
         __syncthreads();
         if (threadIdx.x == 0) {
             const double *en_warp = reinterpret_cast<const double *>(smem + S::EN_OFF);
             double b = 0.0;
             for (int w = 0; w < S::NT / 32; ++w) b += en_warp[w];
-            const unsigned nblk = gridDim.x * gridDim.y;
-            const unsigned id = blockIdx.y * gridDim.x + blockIdx.x;
-            p.energy_part[id] = b;
+            p.energy_part[blockIdx.y * gridDim.x + blockIdx.x] = b;
             __threadfence();
-            if (atomicAdd(p.energy_count, 1u) == nblk - 1) {
-                __threadfence();
-                double e = 0.0;
-                for (unsigned k = 0; k < nblk; ++k) e += *((volatile const double *)p.energy_part + k);
+            last = atomicAdd(p.energy_count, 1u) == nblk - 1;
+        }
+        __syncthreads();
+        if (last) {                                  // uniform over the block
+            __threadfence();
+            double acc = 0.0;
+            for (unsigned k = threadIdx.x; k < nblk; k += S::NT) acc += __ldcg(p.energy_part + k);
+            red[threadIdx.x] = acc;
+            __syncthreads();
+#pragma unroll
+            for (int w = S::NT / 2; w > 0; w >>= 1) {
+                if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) {
                 const int64_t m = n - p.rec_n0;
-                if (m >= 0 && m < p.rec_cap) p.energy[m] = e;
+                if (m >= 0 && m < p.rec_cap) p.energy[m] = red[0];
                 *p.energy_count = 0u;
             }
         }
