@@ -602,6 +602,10 @@ def main():
                   else f"sweep_two_step_kernel<{R},{t.tx},{t.ty}>" if two
                   else f"sweep_tiled_kernel<{R},{t.tx},{t.ty}>" if args.storage == "fp32"
                   else f"sweep_tiled_kernel<{R},{t.tx},{t.ty},{etype}>")
+    rec_variant = args.record in ("energy", "both")
+    if t.kernel == st.STENCIL_KERNEL_TILED and (rec_variant or args.absorb > 0):
+        # the energy and absorbing instantiations are kernels of their own
+        kernel_tag = f"sweep_tiled_kernel<{R},{t.tx},{t.ty},{etype},{int(rec_variant)},{int(args.absorb > 0)}>"
     # point updates per launch of the timed kernel, and its own algorithmic
     # bytes per update: the two-step kernel reads u^n, u^{n-1}, kappa and
     # writes u^{n+1}, u^{n+2} (20 B per two updates)

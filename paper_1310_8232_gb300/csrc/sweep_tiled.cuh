@@ -409,10 +409,17 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                             const float4 ym = col[R + h - r];
                             const float4 yp = col[R + h + r];
                             const float4 zm = uq[h][(K + S::RING - r) % S::RING];   // plane i - r (true values)
-                            float2 sA =
-                                __fadd2_rn(make_float2(row[8 - r], row[9 - r]), make_float2(row[8 + r], row[9 + r]));
-                            float2 sB =
-                                __fadd2_rn(make_float2(row[10 - r], row[11 - r]), make_float2(row[10 + r], row[11 + r]));
+                            float2 sA, sB;
+                            if (r % 2 == 0) {
+                                sA = __fadd2_rn(make_float2(row[8 - r], row[9 - r]),
+                                                make_float2(row[8 + r], row[9 + r]));
+                                sB = __fadd2_rn(make_float2(row[10 - r], row[11 - r]),
+                                                make_float2(row[10 + r], row[11 + r]));
+                            } else {
+                                // odd shifts pair values across register pairs: add them singly
+                                sA = make_float2(row[8 - r] + row[8 + r], row[9 - r] + row[9 + r]);
+                                sB = make_float2(row[10 - r] + row[10 + r], row[11 - r] + row[11 + r]);
+                            }
                             sA = __fadd2_rn(sA, __fadd2_rn(lo2(ym), lo2(yp)));
                             sB = __fadd2_rn(sB, __fadd2_rn(hi2(ym), hi2(yp)));
                             const float2 cr = make_float2(wf<R>(r), wf<R>(r));
