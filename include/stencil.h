@@ -147,8 +147,9 @@ typedef struct {
                                     u^{-1} = 0) and writes kappa into [2]; u^n is then in
                                     user_buffers[stats.current_buffer].  They stay the caller's
                                     and must outlive the plan; the shot server does not take them. */
-    int32_t absorb_width;        /* absorbing layer: points from each face (0 = none, the plain
-                                    ghost-zero boundary); FP32 storage only (16-bit storage is
+    int32_t absorb_width;        /* absorbing layer: points from each face, 0..255 (0 = none, the
+                                    plain ghost-zero boundary; larger: STENCIL_EINVAL); FP32
+                                    storage only (16-bit storage is
                                     refused with STENCIL_EUNSUPPORTED).  The tiled kernel applies
                                     it inside the sweep (single plans, batches, the shot server);
                                     the naive kernel as a save of u^{n-1} on the layer before

@@ -108,22 +108,64 @@ struct SweepParams {
     const float2 *absorb_tab;
 };
 
-// The layer on 4 consecutive points (x = gx..gx+3) of row y, plane z.
-__device__ __forceinline__ void absorb4(int W, const float2 *tab, int nx, int ny, int nz, int gx, int y, int z,
-                                        float4 &v, const float4 &prev)
+// Widest absorbing layer: its damping table (W + 1 entries) is staged in
+// shared memory by every block of the absorbing sweep.
+constexpr int ABSORB_MAX_W = 255;
+
+// Distance of coordinate a to the nearer face of [0, n), clamped to [0, W]
+// (a outside the grid, such as a row's padding, gives 0: written, never read).
+__device__ __forceinline__ int absorb_dist(int a, int n, int W) { return max(0, min(W, min(a, n - 1 - a))); }
+
+// What a thread's 4 consecutive points (x = gx..gx+3) need of the layer for
+// its whole z-march: their x distances, 16 bits each, and whether all four
+// are at least W from both x faces.
+struct AbsorbX {
+    unsigned x01 = 0, x23 = 0;
+    bool inner = true;
+};
+__device__ __forceinline__ AbsorbX absorb_x(int gx, int nx, int W)
 {
-    if (W <= 0) return;                       // a shot without a layer in a grouped launch
+    AbsorbX a;
+    a.x01 = (unsigned)absorb_dist(gx, nx, W) | (unsigned)absorb_dist(gx + 1, nx, W) << 16;
+    a.x23 = (unsigned)absorb_dist(gx + 2, nx, W) | (unsigned)absorb_dist(gx + 3, nx, W) << 16;
+    a.inner = gx >= W && gx + 3 <= nx - 1 - W;
+    return a;
+}
+
+// The same from the coordinates alone (point gx..gx+3 of row y, plane z),
+// for kernels with no registers to spare for the distances above.
+__device__ __forceinline__ void absorb4_at(int W, const float2 *tab, int nx, int ny, int nz, int gx, int y, int z,
+                                           float4 &v, const float4 &prev)
+{
+    if (W <= 0) return;
     const int dyz = min(min(z, nz - 1 - z), min(y, ny - 1 - y));
     if (dyz >= W && gx >= W && gx + 3 <= nx - 1 - W) return;
     float *pv = &v.x;
     const float *pp = &prev.x;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        // x beyond nx (the row's padding) clamps to d = 0: written, never read
         const int d = max(0, min(W, min(dyz, min(gx + j, nx - 1 - gx - j))));
         const float2 t = tab[d];
         pv[j] = fmaf(t.y, pp[j], pv[j] * t.x);
     }
+}
+
+// The layer on the 4 points of one row in one plane: dy = the row's clamped
+// y distance, dz = the plane's z distance; d = min(x, y, z distances).
+__device__ __forceinline__ void absorb4(int W, const float2 *tab, const AbsorbX &ax, int dy, int dz, float4 &v,
+                                        const float4 &prev)
+{
+    if (W <= 0) return;                       // a shot without a layer in a grouped launch
+    const int dyz = min(dy, dz);              // <= W: dy is clamped
+    if (dyz >= W && ax.inner) return;
+    const float2 t0 = tab[min(dyz, (int)(ax.x01 & 0xffffu))];
+    const float2 t1 = tab[min(dyz, (int)(ax.x01 >> 16))];
+    const float2 t2 = tab[min(dyz, (int)(ax.x23 & 0xffffu))];
+    const float2 t3 = tab[min(dyz, (int)(ax.x23 >> 16))];
+    v.x = fmaf(t0.y, prev.x, v.x * t0.x);
+    v.y = fmaf(t1.y, prev.y, v.y * t1.x);
+    v.z = fmaf(t2.y, prev.z, v.z * t2.x);
+    v.w = fmaf(t3.y, prev.w, v.w * t3.x);
 }
 
 // The per-step work of a migration served in a group (reverse-time

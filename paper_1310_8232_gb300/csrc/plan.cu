@@ -613,8 +613,9 @@ int validate_desc(const stencil_desc *d)
         return fail(STENCIL_EINVAL, "graph_steps must be 0 or a positive even number");
     if (d->tune_mode < STENCIL_TUNE_NONE || d->tune_mode > STENCIL_TUNE_EXHAUSTIVE)
         return fail(STENCIL_EINVAL, "bad tune_mode");
-    if (d->absorb_width < 0 || !(d->absorb_eta >= 0.0) || !std::isfinite(d->absorb_eta))
-        return fail(STENCIL_EINVAL, "absorb_width must be >= 0 and absorb_eta finite and >= 0");
+    if (d->absorb_width < 0 || d->absorb_width > ABSORB_MAX_W || !(d->absorb_eta >= 0.0) ||
+        !std::isfinite(d->absorb_eta))
+        return fail(STENCIL_EINVAL, "absorb_width must be in [0, %d] and absorb_eta finite and >= 0", ABSORB_MAX_W);
     const int n_user = (d->user_buffers[0] != nullptr) + (d->user_buffers[1] != nullptr) +
                        (d->user_buffers[2] != nullptr);
     if (n_user) {

@@ -212,7 +212,10 @@ __device__ __forceinline__ float4 scale4(const float4 &v, float s)
 // One block's work: tile (bx, by) of the xy plane, output planes [z0, z1)
 // of one shot, at time level n.  map_* are the shot's tensor maps (kernel
 // parameters or 64-byte aligned global memory).
-template <int R, int TX, int TY, typename E, bool REC, bool ABS = false>
+// ABS_HOIST: with the layer, keep the thread's distances to the faces in
+// registers for the whole z-march (the single-shot kernel) or recompute them
+// per point (the grouped kernel, which has no registers to spare).
+template <int R, int TX, int TY, typename E, bool REC, bool ABS = false, bool ABS_HOIST = true>
 __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUtensorMap *map_up,
                                            const CUtensorMap *map_k, const SweepParams &params, int bx, int by,
                                            int z0, int z1, int64_t n_level, unsigned char *smem)
@@ -324,6 +327,23 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     // launch: evaluated once, outside the unrolled plane loop)
     float src_add = 0.0f;
     if (src_here) src_add = (float)(p.src.scale * ricker(p.src.f, p.src.t0, (double)n_level * p.src.dt));
+
+    // ABS: the layer's damping table in shared memory, the x distances of the
+    // thread's points and the y distances of its rows (fixed for the whole
+    // z-march)
+    AbsorbX abs_x;
+    int abs_dy[S::ROWS];
+    __shared__ float2 abs_tab[ABS ? ABSORB_MAX_W + 1 : 1];
+    if constexpr (ABS) {
+        if (p.absorb_w > 0)                   // a shot of a grouped launch may have none
+            for (int j = tid; j <= p.absorb_w; j += S::NT) abs_tab[j] = p.absorb_tab[j];
+        __syncthreads();
+        if constexpr (ABS_HOIST) {
+            abs_x = absorb_x(gx, p.nx, p.absorb_w);
+#pragma unroll
+            for (int h = 0; h < S::ROWS; ++h) abs_dy[h] = absorb_dist(gy0 + h, p.ny, p.absorb_w);
+        }
+    }
 
     // ring slot j holds, per row, plane i's u values and output i's partial
     // sum for the planes i with i mod RING == j (i counts planes from z0 - R)
@@ -476,8 +496,12 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
                         const float2 oB =
                             __ffma2_rn(hi2(kap[h]), fB, __ffma2_rn(neg1, hi2(prev[h]), __fmul2_rn(two, hi2(cc))));
                         float4 nxt = make_float4(oA.x, oA.y, oB.x, oB.y);
-                        if constexpr (ABS)
-                            absorb4(p.absorb_w, p.absorb_tab, p.nx, p.ny, p.nz, gx, gy0 + h, o, nxt, prev[h]);
+                        if constexpr (ABS) {
+                            if constexpr (ABS_HOIST)
+                                absorb4(p.absorb_w, abs_tab, abs_x, abs_dy[h], min(o, p.nz - 1 - o), nxt, prev[h]);
+                            else
+                                absorb4_at(p.absorb_w, abs_tab, p.nx, p.ny, p.nz, gx, gy0 + h, o, nxt, prev[h]);
+                        }
                         if (src_here && src_row == h && o == p.src.z) {
                             const int k = p.src.x - gx;
                             if (k == 0) nxt.x += src_add;
@@ -832,7 +856,7 @@ __global__ void __launch_bounds__(TiledShape<R, TX, TY, E>::NT, TiledShape<R, TX
         fence_tensormap(&g.core[par ^ 1]);
         fence_tensormap(&g.kcore);
     }
-    sweep_tile<R, TX, TY, E, false, ABS>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n,
+    sweep_tile<R, TX, TY, E, false, ABS, false>(&g.halo[par], &g.core[par ^ 1], &g.kcore, p, it.bx, it.by, it.z0, it.z1, n,
                                          smem);
 }
 

@@ -83,6 +83,7 @@ def _desc(st, **kw):
 @pytest.mark.parametrize("field,value", [
     ("nx", 0), ("ny", -1), ("radius", 3), ("radius", 6), ("dx", 0.0), ("dt", -1.0),
     ("src_x", 8), ("src_z", -1), ("graph_steps", 3), ("tune_mode", 9),
+    ("absorb_width", -1), ("absorb_width", 256),
 ])
 def test_invalid_descriptors_rejected_before_device(st, field, value):
     d, v = _desc(st, **{field: value})
