@@ -204,6 +204,12 @@ __device__ __forceinline__ int64_t current_step(const SweepParams &p)
     return *p.step_base + p.step_off;
 }
 
+// A kernel launched as a programmatic dependent of the previous one in its
+// stream (cudaLaunchAttributeProgrammaticStreamSerialization) may start while
+// that one drains; this waits until it has completed and its writes are
+// visible.  Without the attribute it returns at once.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---- PTX wrappers (mbarrier + TMA; sm_90 and later, used on sm_103a) ----
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {

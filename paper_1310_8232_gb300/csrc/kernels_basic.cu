@@ -12,17 +12,25 @@ namespace stencil {
 // K0: one thread per grid point; every neighbour is read from global memory
 // with an explicit bounds test (ghost zeros).  The GPU counterpart of the
 // paper's "No-Blocksize" variant (Sec. 3.1): no data staging at all.
-// grid (ceil(nx/128), ny, nz), 128 threads.
+// 128 threads a block: TXN = nx rounded up to a warp (at most 128) along x
+// times 128 / TXN rows, so a narrow grid does not leave most threads idle;
+// grid (ceil(nx/TXN), ceil(ny/(128/TXN)), nz).  Each step is launched as a
+// programmatic dependent of the previous one: its blocks are scheduled while
+// that step drains and wait before touching memory, which hides most of the
+// launch latency on the small grids this kernel serves.
 // ---------------------------------------------------------------------------
 template <int R, bool REC>
 __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
 {
+    grid_dependency_wait();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (!REC && x >= p.nx) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const bool in = x < p.nx && y < p.ny;
+    if (!REC && !in) return;
     float e = 0.0f;                           // REC: this point's energy term
-    if (x < p.nx) {
+    if (in) {
         const int64_t q = (int64_t)z * p.plane + (int64_t)y * p.pitch + x;
         const float *u = static_cast<const float *>(p.u);
         float *up = static_cast<float *>(p.up);
@@ -57,10 +65,10 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
         __shared__ int last;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (double)e;
+        if ((tid & 31) == 0) wsum[tid >> 5] = (double)e;
         __syncthreads();
         const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             const unsigned id = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
             p.energy_part[id] = ((wsum[0] + wsum[1]) + wsum[2]) + wsum[3];
             __threadfence();
@@ -71,14 +79,14 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
             __threadfence();
             __shared__ double tsum[128];
             double a = 0.0;
-            for (unsigned k = threadIdx.x; k < nblk; k += 128) a += *((volatile const double *)p.energy_part + k);
-            tsum[threadIdx.x] = a;
+            for (unsigned k = tid; k < nblk; k += 128) a += *((volatile const double *)p.energy_part + k);
+            tsum[tid] = a;
             __syncthreads();
             for (int w = 64; w > 0; w >>= 1) {
-                if (threadIdx.x < w) tsum[threadIdx.x] += tsum[threadIdx.x + w];
+                if (tid < w) tsum[tid] += tsum[tid + w];
                 __syncthreads();
             }
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 const int64_t m = current_step(p) - p.rec_n0;
                 if (m >= 0 && m < p.rec_cap) p.energy[m] = tsum[0];
                 *p.energy_count = 0u;
@@ -89,20 +97,26 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
 
 cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)
 {
-    if (p.ny > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
-    dim3 grid((p.nx + 127) / 128, p.ny, p.nz);
+    const int txn = std::min(128, (p.nx + 31) / 32 * 32);
+    const int tyn = 128 / txn;
+    const int gy = (p.ny + tyn - 1) / tyn;
+    if (gy > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((p.nx + txn - 1) / txn, gy, p.nz);
+    cfg.blockDim = dim3(txn, tyn, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     const bool rec = p.energy_on != 0;
-    if (R == 4 && rec)
-        sweep_naive_kernel<4, true><<<grid, 128, 0, s>>>(p);
-    else if (R == 4)
-        sweep_naive_kernel<4, false><<<grid, 128, 0, s>>>(p);
-    else if (R == 5 && rec)
-        sweep_naive_kernel<5, true><<<grid, 128, 0, s>>>(p);
-    else if (R == 5)
-        sweep_naive_kernel<5, false><<<grid, 128, 0, s>>>(p);
-    else
-        return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    if (R == 4 && rec) return cudaLaunchKernelEx(&cfg, sweep_naive_kernel<4, true>, p);
+    if (R == 4) return cudaLaunchKernelEx(&cfg, sweep_naive_kernel<4, false>, p);
+    if (R == 5 && rec) return cudaLaunchKernelEx(&cfg, sweep_naive_kernel<5, true>, p);
+    if (R == 5) return cudaLaunchKernelEx(&cfg, sweep_naive_kernel<5, false>, p);
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------

@@ -65,6 +65,7 @@ int stencil_record_start(stencil_plan_t h, const stencil_record_cfg *c)
     // the sweep's grid: one energy partial per block
     int64_t blocks;
     if (p->tile.kernel == STENCIL_KERNEL_NAIVE) {
+        // at least its blocks: 128 x 1 each, or narrower and taller on narrow grids
         blocks = (int64_t)((p->nx + 127) / 128) * p->ny * p->nz;
     } else {
         const int zc = p->tile.zchunk > 0 ? p->tile.zchunk : p->nz;
