@@ -344,9 +344,10 @@ cudaError_t launch_group_advance(GroupShot *shots, int n_shots, int k, cudaStrea
 // of step n = *step_base + step_off; blockIdx.y picks the shot from `list`.
 // On most steps only the receiver rows are touched (record going forward,
 // injection of the reversed traces going back); on the steps whose field is
-// a snapshot time the blocks sweep the whole field, each thread doing the
-// receiver-row work of its point first, then the snapshot copy (forward) or
-// the imaging condition (backward).  The arithmetic is that of the single
+// a snapshot time the blocks sweep the whole field, the receiver-row work of
+// a row first, then the snapshot copy (forward) or the imaging condition
+// (backward).  One warp per row (no index division per point), 16-byte
+// accesses where the rows allow them.  The arithmetic is that of the single
 // plan's record, injection and imaging kernels: a copy, u += 1 * trace, and
 // img = fmaf(scale * s, u, img).
 __global__ void group_rtm_kernel(const GroupShot *shots, const int *list, int step_off)
@@ -364,30 +365,58 @@ __global__ void group_rtm_kernel(const GroupShot *shots, const int *list, int st
     const int64_t tb = o.T - n;                         // backward: forward time of the field after this step
     const bool field = fwd ? (n + 1) % o.k == 0 : (tb % o.k == 0 && tb >= o.k);
     const float inj_scale = 1.0f;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (!field) {
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < per; t += stride) {
-            const int r = (int)(t / nx), x = (int)(t - (int64_t)r * nx);
-            const int64_t q = o.z * plane + (int64_t)(o.y < 0 ? r : o.y) * pitch + x;
-            if (fwd) o.traces[n * per + t] = u[q];
-            else u[q] += inj_scale * o.traces[(o.T - 1 - n) * per + t];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float *trace = o.traces + (fwd ? n : o.T - 1 - n) * per;   // this step's trace
+    // one receiver row: record (u -> trace) or inject (u += trace)
+    auto receiver_row = [&](float *ur, float *tr) {
+        for (int x = lane; x < nx; x += 32) {
+            if (fwd) tr[x] = ur[x];
+            else ur[x] += inj_scale * tr[x];
         }
+    };
+    if (!field) {
+        for (int64_t r = warp; r < rows; r += n_warps)
+            receiver_row(u + o.z * plane + (int64_t)(o.y < 0 ? (int)r : o.y) * pitch, trace + r * nx);
         return;
     }
     const int64_t pts = (int64_t)nx * ny * nz, sl = fwd ? (n + 1) / o.k - 1 : tb / o.k - 1;
     float *snap = o.snaps + sl * pts;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pts; i += stride) {
-        const int64_t row = i / nx;
-        const int x = (int)(i - row * nx);
+    // snapshots and the image are dense (row r at r * nx); u is pitched
+    const bool vec = (nx & 3) == 0 && (pitch & 3) == 0 && (reinterpret_cast<uintptr_t>(snap) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(o.image) & 15) == 0 && (reinterpret_cast<uintptr_t>(u) & 15) == 0;
+    const int64_t all_rows = (int64_t)ny * nz;
+    for (int64_t row = warp; row < all_rows; row += n_warps) {
         const int z = (int)(row / ny), y = (int)(row - (int64_t)z * ny);
-        const int64_t q = row * pitch + x;
+        float *ur = u + row * pitch;
+        float *sr = snap + row * nx;
+        float *ir = o.image + row * nx;
         if (z == o.z && (o.y < 0 || y == o.y)) {
-            const int64_t t = (int64_t)(o.y < 0 ? y : 0) * nx + x;
-            if (fwd) o.traces[n * per + t] = u[q];
-            else u[q] += inj_scale * o.traces[(o.T - 1 - n) * per + t];
+            receiver_row(ur, trace + (int64_t)(o.y < 0 ? y : 0) * nx);
+            __syncwarp();                               // the imaging below reads the injected row
         }
-        if (fwd) snap[i] = u[q];
-        else o.image[i] = fmaf(o.image_scale * snap[i], u[q], o.image[i]);
+        if (vec) {
+            for (int x4 = lane; x4 < nx / 4; x4 += 32) {
+                const float4 uv = reinterpret_cast<const float4 *>(ur)[x4];
+                if (fwd) {
+                    reinterpret_cast<float4 *>(sr)[x4] = uv;
+                } else {
+                    const float4 sv = reinterpret_cast<const float4 *>(sr)[x4];
+                    float4 iv = reinterpret_cast<const float4 *>(ir)[x4];
+                    iv.x = fmaf(o.image_scale * sv.x, uv.x, iv.x);
+                    iv.y = fmaf(o.image_scale * sv.y, uv.y, iv.y);
+                    iv.z = fmaf(o.image_scale * sv.z, uv.z, iv.z);
+                    iv.w = fmaf(o.image_scale * sv.w, uv.w, iv.w);
+                    reinterpret_cast<float4 *>(ir)[x4] = iv;
+                }
+            }
+        } else {
+            for (int x = lane; x < nx; x += 32) {
+                if (fwd) sr[x] = ur[x];
+                else ir[x] = fmaf(o.image_scale * sr[x], ur[x], ir[x]);
+            }
+        }
     }
 }
 
@@ -410,18 +439,33 @@ namespace stencil {
 
 // ---------------------------------------------------------------------------
 // Zero-lag cross-correlation imaging condition: img += scale * s * u over a
-// dense (s, img) and a pitched u grid; 4 points per thread where the row
-// allows it.  HBM-bound: 16 B per point.
+// dense (s, img) and a pitched u grid.  One warp per row (no index division
+// per point), 16-byte accesses when every row of the three arrays starts on
+// a 16-byte boundary.  HBM-bound: 16 B per point.
 // ---------------------------------------------------------------------------
 __global__ void image_accumulate_kernel(const float *s, const float *u, float *img, int nx, int64_t rows,
-                                        int64_t pitch, float scale)
+                                        int64_t pitch, float scale, int vec)
 {
-    const int64_t total = rows * nx;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t row = i / nx;
-        const int x = (int)(i - row * nx);
-        img[i] = fmaf(scale * s[i], u[row * pitch + x], img[i]);
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < rows; row += n_warps) {
+        const float *sr = s + row * nx;
+        const float *ur = u + row * pitch;
+        float *ir = img + row * nx;
+        if (vec) {
+            for (int x4 = lane; x4 < nx / 4; x4 += 32) {
+                const float4 sv = reinterpret_cast<const float4 *>(sr)[x4];
+                const float4 uv = reinterpret_cast<const float4 *>(ur)[x4];
+                float4 iv = reinterpret_cast<const float4 *>(ir)[x4];
+                iv.x = fmaf(scale * sv.x, uv.x, iv.x);
+                iv.y = fmaf(scale * sv.y, uv.y, iv.y);
+                iv.z = fmaf(scale * sv.z, uv.z, iv.z);
+                iv.w = fmaf(scale * sv.w, uv.w, iv.w);
+                reinterpret_cast<float4 *>(ir)[x4] = iv;
+            }
+        } else {
+            for (int x = lane; x < nx; x += 32) ir[x] = fmaf(scale * sr[x], ur[x], ir[x]);
+        }
     }
 }
 
@@ -429,10 +473,11 @@ cudaError_t launch_image_accumulate(const float *s, const float *u, float *img, 
                                     int64_t pitch, float scale, cudaStream_t st)
 {
     const int64_t rows = (int64_t)ny * nz;
-    const int64_t total = rows * nx;
-    const int64_t want = (total + 255) / 256;
-    const int blocks = (int)std::min<int64_t>(want, 152 * 16);
-    image_accumulate_kernel<<<blocks, 256, 0, st>>>(s, u, img, nx, rows, pitch, scale);
+    const int64_t want = (rows + 7) / 8;                 // 8 warps a block, one row each per pass
+    const int blocks = (int)std::min<int64_t>(want, 152 * 8);
+    const int vec = (nx % 4 == 0) && (pitch % 4 == 0) && reinterpret_cast<uintptr_t>(s) % 16 == 0 &&
+                    reinterpret_cast<uintptr_t>(u) % 16 == 0 && reinterpret_cast<uintptr_t>(img) % 16 == 0;
+    image_accumulate_kernel<<<blocks, 256, 0, st>>>(s, u, img, nx, rows, pitch, scale, vec);
     return cudaGetLastError();
 }
 
