@@ -12,15 +12,17 @@ namespace stencil {
 // K0: one thread per grid point; every neighbour is read from global memory
 // with an explicit bounds test (ghost zeros).  The GPU counterpart of the
 // paper's "No-Blocksize" variant (Sec. 3.1): no data staging at all.
-// 128 threads a block: TXN = nx rounded up to a warp (at most 128) along x
-// times 128 / TXN rows, so a narrow grid does not leave most threads idle;
-// grid (ceil(nx/TXN), ceil(ny/(128/TXN)), nz).  Each step is launched as a
+// NAIVE_NT threads a block: TXN = nx rounded up to a warp (at most 128)
+// along x times NAIVE_NT / TXN rows, so a narrow grid does not leave most
+// threads idle; grid (ceil(nx/TXN), ceil(ny/(NAIVE_NT/TXN)), nz).  Each step is launched as a
 // programmatic dependent of the previous one: its blocks are scheduled while
 // that step drains and wait before touching memory, which hides most of the
 // launch latency on the small grids this kernel serves.
 // ---------------------------------------------------------------------------
+constexpr int NAIVE_NT = 128;
+
 template <int R, bool REC>
-__global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
+__global__ void __launch_bounds__(NAIVE_NT) sweep_naive_kernel(SweepParams p)
 {
     grid_dependency_wait();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -59,9 +61,9 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
         }
     }
     if (REC && p.energy_on) {
-        // block partial (FP32 per warp, FP64 over the 4 warps), then the last
-        // block adds every partial in a fixed order with all its threads
-        __shared__ double wsum[4];
+        // block partial (FP32 per warp, FP64 over the warps in order), then
+        // the last block adds every partial in a fixed order with all its threads
+        __shared__ double wsum[NAIVE_NT / 32];
         __shared__ int last;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
@@ -70,19 +72,21 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
         const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
         if (tid == 0) {
             const unsigned id = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-            p.energy_part[id] = ((wsum[0] + wsum[1]) + wsum[2]) + wsum[3];
+            double b = 0.0;
+            for (int w = 0; w < NAIVE_NT / 32; ++w) b += wsum[w];
+            p.energy_part[id] = b;
             __threadfence();
             last = atomicAdd(p.energy_count, 1u) == nblk - 1;
         }
         __syncthreads();
         if (last) {
             __threadfence();
-            __shared__ double tsum[128];
+            __shared__ double tsum[NAIVE_NT];
             double a = 0.0;
-            for (unsigned k = tid; k < nblk; k += 128) a += *((volatile const double *)p.energy_part + k);
+            for (unsigned k = tid; k < nblk; k += NAIVE_NT) a += *((volatile const double *)p.energy_part + k);
             tsum[tid] = a;
             __syncthreads();
-            for (int w = 64; w > 0; w >>= 1) {
+            for (int w = NAIVE_NT / 2; w > 0; w >>= 1) {
                 if (tid < w) tsum[tid] += tsum[tid + w];
                 __syncthreads();
             }
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(128) sweep_naive_kernel(SweepParams p)
 cudaError_t launch_naive(int R, const SweepParams &p, cudaStream_t s)
 {
     const int txn = std::min(128, (p.nx + 31) / 32 * 32);
-    const int tyn = 128 / txn;
+    const int tyn = NAIVE_NT / txn;
     const int gy = (p.ny + tyn - 1) / tyn;
     if (gy > 65535 || p.nz > 65535) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
