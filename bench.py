@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -92,10 +93,15 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the dominant kernel's code (comments and whitespace removed, so
+    that a note in the source does not invalidate the recorded traffic)."""
     h = hashlib.sha256()
     for name in ("sweep_tiled.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1310_8232_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1310_8232_gb300", "csrc", name), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -196,7 +196,8 @@ STENCIL_API void stencil_desc_init(stencil_desc *d);
 
 /* Build a plan on the current CUDA device: validate *d, allocate the two
  * wavefield buffers and kappa on the device, compute kappa = v^2 dt^2/dx^2
- * and vmax there, check vmax*dt/dx against the CFL bound (STENCIL_ECFL),
+ * (FP32, within 1 ulp of the FP64 product rounded once) and vmax there,
+ * check vmax*dt/dx against the CFL bound (STENCIL_ECFL),
  * zero u^0 and u^{-1}, and pick the tile (tune_mode).  Synchronous.  The
  * velocity array is only read during this call. */
 STENCIL_API int stencil_plan(const stencil_desc *d, stencil_plan_t *out);

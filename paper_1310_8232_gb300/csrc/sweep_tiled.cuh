@@ -365,7 +365,7 @@ __device__ __forceinline__ void sweep_tile(const CUtensorMap *map_u, const CUten
     // REC: this thread's energy terms, FP32 over each group of RING planes,
     // then FP64 over the z-chunk; one warp sum at the end.  Points outside the
     // grid add exactly zero: their u^{n+1} and u^n are zero (zero-filled
-    // inputs, kappa = 0 there), and 1/kappa is taken of max(kappa, FLT_MIN),
+    // inputs, kappa = 0 there), and 1/kappa is taken of kappa + FLT_MIN,
     // which keeps 0 * (1/kappa) finite, so no point needs a mask.
     double eacc = 0.0;
 
