@@ -92,17 +92,25 @@ def measured_peaks():
         return None
 
 
-def kernel_source_hash() -> str:
-    """Hash of the dominant kernel's code (comments and whitespace removed, so
-    that a note in the source does not invalidate the recorded traffic)."""
+def code_digest(texts) -> str:
+    """16 hex digits of SHA-256 over C/C++ sources with comments and
+    whitespace runs removed: a change of code changes it, a note does not."""
     h = hashlib.sha256()
-    for name in ("sweep_tiled.cuh", "common.cuh"):
-        with open(os.path.join(ROOT, "paper_1310_8232_gb300", "csrc", name), encoding="utf-8") as fh:
-            text = fh.read()
+    for text in texts:
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_hash() -> str:
+    """Digest of the dominant kernel's code (sweep_tiled.cuh, common.cuh), the
+    key of the recorded traffic in profiles/traffic.txt."""
+    texts = []
+    for name in ("sweep_tiled.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1310_8232_gb300", "csrc", name), encoding="utf-8") as fh:
+            texts.append(fh.read())
+    return code_digest(texts)
 
 
 def profiled_traffic(kernel_tag: str):
