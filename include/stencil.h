@@ -228,7 +228,11 @@ STENCIL_API int stencil_get_field(stencil_plan_t p, int32_t which, float *out, i
 
 /* Set the state: u^n = u, u^{n-1} = u_prev (dense FP32; NULL = zeros), and
  * the step counter n = step (16-bit storage keeps u^n and d^n = u^n -
- * u^{n-1}, each rounded once with its plane's scale).  Synchronous. */
+ * u^{n-1}, each rounded once with its plane's scale).  Synchronous when it
+ * copies from host memory (the arrays may be reused on return).  With
+ * device arrays or NULLs it only enqueues the work on the plan's stream:
+ * device arrays must stay unchanged until the stream has passed the copy,
+ * and device-side errors are reported by the next synchronising call. */
 STENCIL_API int stencil_set_fields(stencil_plan_t p, const float *u, const float *u_prev,
                        int32_t on_device, int64_t step);
 

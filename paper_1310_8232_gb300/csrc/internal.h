@@ -32,6 +32,10 @@ cudaError_t launch_sqdiff(const float *a, const double *b, int nx, int ny, int n
 
 // n += k on the device (step counter between launch chunks)
 cudaError_t launch_advance(int64_t *n, int k, cudaStream_t s);
+// n = v on the device, in stream order (no host staging of the value)
+cudaError_t launch_set_step(int64_t *n, int64_t v, cudaStream_t s);
+// a[0..n) = b[0..n) = 0 and *step = v, one launch
+cudaError_t launch_clear_levels(float *a, float *b, int64_t n, int64_t *step, int64_t v, cudaStream_t s);
 
 // ---- per-step operations around the plain sweep (plane_ops.cu) ----
 struct StepOps {

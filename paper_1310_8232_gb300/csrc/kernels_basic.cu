@@ -326,6 +326,28 @@ cudaError_t launch_sqdiff(const float *a, const double *b, int nx, int ny, int n
 }
 
 __global__ void advance_kernel(int64_t *n, int k) { *n += k; }
+__global__ void set_step_kernel(int64_t *n, int64_t v) { *n = v; }
+
+// Zero two FP32 arrays of n elements (16-byte aligned when vec) and set the
+// step counter: the reset of a plan's two levels in one launch.
+__global__ void clear_levels_kernel(float *a, float *b, int64_t n, int vec, int64_t *step, int64_t v)
+{
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (i0 == 0) *step = v;
+    if (vec) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t i = i0; i < n / 4; i += stride) {
+            reinterpret_cast<float4 *>(a)[i] = z;
+            reinterpret_cast<float4 *>(b)[i] = z;
+        }
+    } else {
+        for (int64_t i = i0; i < n; i += stride) {
+            a[i] = 0.0f;
+            b[i] = 0.0f;
+        }
+    }
+}
 
 // each shot's counter moves k steps, but never past its last step
 __global__ void group_advance_kernel(GroupShot *shots, int n_shots, int k)
@@ -428,6 +450,21 @@ cudaError_t launch_group_rtm(const GroupShot *shots, const int *list, int n_list
 {
     if (n_list <= 0) return cudaSuccess;
     group_rtm_kernel<<<dim3(152 * 8, n_list), 256, 0, s>>>(shots, list, step_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clear_levels(float *a, float *b, int64_t n, int64_t *step, int64_t v, cudaStream_t s)
+{
+    const int vec = n % 4 == 0 && reinterpret_cast<uintptr_t>(a) % 16 == 0 && reinterpret_cast<uintptr_t>(b) % 16 == 0;
+    const int64_t work = vec ? n / 4 : n;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 8));
+    clear_levels_kernel<<<blocks, 256, 0, s>>>(a, b, n, vec, step, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(int64_t *n, int64_t v, cudaStream_t s)
+{
+    set_step_kernel<<<1, 1, 0, s>>>(n, v);
     return cudaGetLastError();
 }
 

@@ -943,6 +943,14 @@ int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, in
     Plan *p = reinterpret_cast<Plan *>(h);
     cudaSetDevice(p->dev);
     const float *src[2] = {u, u_prev};
+    if (p->storage == STENCIL_FP32 && !u && !u_prev) {
+        // both levels zero: one launch clears them and sets the counter
+        cudaError_t e = launch_clear_levels(static_cast<float *>(p->level_buf(0)), static_cast<float *>(p->level_buf(1)),
+                                            p->field_elems, p->d_step, step, p->stream);
+        if (e != cudaSuccess) return fail_cuda(e, "field reset");
+        p->steps_done = step;
+        return STENCIL_OK;
+    }
     if (p->storage != STENCIL_FP32) {
         int rc = p->ensure_staging();
         if (rc) return rc;
@@ -978,10 +986,14 @@ int stencil_set_fields(stencil_plan_t h, const float *u, const float *u_prev, in
         }
         if (e != cudaSuccess) return fail_cuda(e, "amax reset");
     }
-    cudaError_t e = cudaMemcpyAsync(p->d_step, &step, sizeof step, cudaMemcpyHostToDevice, p->stream);
-    if (e != cudaSuccess) return fail_cuda(e, "step counter copy");
+    cudaError_t e = launch_set_step(p->d_step, step, p->stream);
+    if (e != cudaSuccess) return fail_cuda(e, "step counter");
     p->steps_done = step;
-    return p->check_device_error();
+    // a copy from host memory is complete before the caller gets its arrays
+    // back; without one the call only enqueues (errors surface at the next
+    // synchronising call)
+    if (!on_device && (u || u_prev)) return p->check_device_error();
+    return STENCIL_OK;
 }
 
 int stencil_set_velocity(stencil_plan_t h, const float *velocity, int32_t on_device)
