@@ -404,3 +404,31 @@ def test_set_velocity_replaces_the_model_with_graphs_captured(env):
             assert np.array_equal(out, fresh(v))
     finally:
         st.stencil_destroy(plan)
+
+
+@pytest.mark.parametrize("tile", [NAIVE, DEFAULT_TILED, (3, 0, 0, -1)])
+def test_reset_to_zero_fields_at_a_step_equals_a_fresh_start(env, tile):
+    """stencil_set_fields with no arrays (one launch clears both levels and
+    sets the step counter, with no host wait): after 7 steps, a reset to
+    step 3 followed by 5 steps gives the fields of a fresh plan set to step 3
+    and run 5 steps, bit for bit (the source term follows the counter)."""
+    torch, st = env
+    nx, ny, nz, R = 52, 37, 29, 5
+    v = workloads.layered_velocity(nx, ny, nz, seed=77)
+    dt = workloads.time_step(oracle.cfl_limit(R), workloads.DX, float(v.max()))
+    out = []
+    for warm in (7, 0):
+        plan = st.stencil_plan(st.make_desc(v, dt, radius=R, tile=tile, graph_steps=2, stream=cur_stream(torch)))
+        try:
+            st.stencil_step(plan, warm)
+            st.stencil_set_fields(plan, None, None, 3)
+            assert st.stencil_get_stats(plan).steps_done == 3
+            u = np.empty_like(v)
+            st.stencil_run(plan, 5, u)
+            um1 = np.empty_like(v)
+            st.stencil_get_field(plan, 1, um1)
+            out.append((u, um1))
+        finally:
+            st.stencil_destroy(plan)
+    assert np.count_nonzero(out[0][0]) > 0
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
