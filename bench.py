@@ -645,6 +645,16 @@ def main():
     else:
         launches_per_shot = sweeps(T) + (T + 63) // 64
         sweeps_per_shot = sweeps(T)
+    # and the work around the sweeps: each shot's reset (stencil_set_fields
+    # with no arrays: one kernel for FP32; the 16-bit pack of both fields, two
+    # kernels each, and the step counter), a receiver record kernel per step,
+    # and, where the layer is not folded into the sweep (naive kernel), its
+    # save and damping passes (three kernels each) and the source kernel
+    launches_per_shot += 1 if args.storage == "fp32" else 5
+    if args.record in ("traces", "both"):
+        launches_per_shot += T
+    if args.absorb > 0 and t.kernel == st.STENCIL_KERNEL_NAIVE:
+        launches_per_shot += 7 * T
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     with ClockSampler(local) as clk:
