@@ -710,6 +710,47 @@ def main():
         e2e = {"value": world * pts_per_shot * args.steps / e2e_s / 1e9, "unit": METRIC,
                "h2d_bytes_per_step": int(hv.numel() * 4), "d2h_bytes_per_step": int(hout.numel() * 4),
                "api": "stencil_set_velocity(host pinned) + stencil_set_fields + stencil_run(out=host pinned)"}
+        if args.record == "none":
+            # The same shots through two plans on their own streams, each
+            # driven by its own host thread, as a caller with many shots would
+            # run them: one plan's copies overlap the other's sweeps.  Each
+            # plan runs --steps shots (2 x --steps in all).
+            import threading
+            stream2 = torch.cuda.Stream()
+            plan2 = st.stencil_plan(st.make_desc(dv, dt, radius=R, dx=workloads.DX, tile=tile,
+                                                 graph_steps=args.graph, stream=stream2.cuda_stream,
+                                                 storage=STORAGE_ID[args.storage],
+                                                 absorb=(args.absorb, 0.2 if args.absorb else 0.0)))
+            hout2 = torch.empty((n, n, n), dtype=torch.float32).pin_memory()
+            errors = []
+
+            def shots(pl, k, out):
+                try:
+                    for _ in range(k):
+                        st.stencil_set_velocity(pl, hv)
+                        st.stencil_set_fields(pl, None, None, 0)
+                        st.stencil_run(pl, T, out)
+                except Exception as ex:          # reported after the join
+                    errors.append(ex)
+
+            shots(plan2, 1, hout2)
+            barrier()
+            t0 = time.perf_counter()
+            workers = [threading.Thread(target=shots, args=(plan, args.steps, hout)),
+                       threading.Thread(target=shots, args=(plan2, args.steps, hout2))]
+            for w in workers:
+                w.start()
+            for w in workers:
+                w.join()
+            barrier()
+            two_s = ranks.max(time.perf_counter() - t0)
+            st.stencil_destroy(plan2)
+            if errors:
+                raise errors[0]
+            e2e["two_plans"] = {
+                "value": world * pts_per_shot * 2 * args.steps / two_s / 1e9, "unit": METRIC,
+                "api": "two plans on their own streams, one host thread each, each shot as above "
+                       "(the copies of one plan overlap the sweeps of the other)"}
     st.stencil_destroy(plan)
 
     cpu = None
