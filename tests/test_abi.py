@@ -84,6 +84,9 @@ def _desc(st, **kw):
     ("nx", 0), ("ny", -1), ("radius", 3), ("radius", 6), ("dx", 0.0), ("dt", -1.0),
     ("src_x", 8), ("src_z", -1), ("graph_steps", 3), ("tune_mode", 9),
     ("absorb_width", -1), ("absorb_width", 256),
+    ("nz", 0), ("ny", 65536), ("nz", 65536), ("nx", (1 << 24) + 1), ("dx", float("inf")), ("dt", float("nan")),
+    ("src_y", 8), ("src_x", -1), ("src_freq_hz", 0.0), ("storage", 3), ("graph_steps", -2),
+    ("absorb_eta", -0.1), ("absorb_eta", float("nan")), ("absorb_eta", float("inf")), ("tune_mode", -1),
 ])
 def test_invalid_descriptors_rejected_before_device(st, field, value):
     d, v = _desc(st, **{field: value})
@@ -167,3 +170,36 @@ def test_tile_info_reports_built_tiles(st):
     assert 0 < smem <= 227 * 1024 and threads % 32 == 0
     assert st.stencil_tile_info(5, 48, 16) is None
     assert st.stencil_tile_info(3, 64, 16) is None
+
+
+@pytest.mark.parametrize("bufs,code", [
+    ((0x10000, 0, 0), "EINVAL"),                     # one of three
+    ((0x10000, 0x20000, 0x20000), "EINVAL"),         # the same buffer twice
+    ((0x10008, 0x20000, 0x30000), "EINVAL"),         # not 16-byte aligned
+])
+def test_user_buffer_descriptors_rejected_before_device(st, bufs, code):
+    """The caller-owned buffer rules are checked on the pointers alone, before
+    any device call (the addresses here are never dereferenced)."""
+    d, v = _desc(st)
+    for i, b in enumerate(bufs):
+        d.user_buffers[i] = b if b else None
+    with pytest.raises(st.StencilError) as ei:
+        st.stencil_plan(d)
+    assert ei.value.code == getattr(st, "STENCIL_" + code)
+
+
+def test_user_buffers_need_whole_16_byte_rows_and_fp32(st):
+    v = np.full((8, 8, 6), 2000.0, dtype=np.float32)      # nx = 6: rows of 24 bytes
+    d = st.make_desc(v, dt=1e-3, radius=4)
+    for i, b in enumerate((0x10000, 0x20000, 0x30000)):
+        d.user_buffers[i] = b
+    with pytest.raises(st.StencilError) as ei:
+        st.stencil_plan(d)
+    assert ei.value.code == st.STENCIL_EINVAL
+    d, v = _desc(st)
+    for i, b in enumerate((0x10000, 0x20000, 0x30000)):
+        d.user_buffers[i] = b
+    d.storage = st.STENCIL_FP16
+    with pytest.raises(st.StencilError) as ei:
+        st.stencil_plan(d)
+    assert ei.value.code == st.STENCIL_EUNSUPPORTED
