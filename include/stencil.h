@@ -28,8 +28,10 @@
  *   - the caller owns every array it passes; a plan copies what it keeps;
  *   - a pointer flagged "on device" is a CUDA device pointer on the device
  *     that was current when the plan was made; otherwise it is host memory;
- *   - a plan is used by one host thread at a time; a shot server is
- *     thread-safe.
+ *   - a plan is used by one host thread at a time; different plans (each
+ *     on its own stream) may be driven from different threads at once, and
+ *     a call that waits waits only for its own plan's stream; a shot server
+ *     is thread-safe.
  */
 #ifndef STENCIL_H
 #define STENCIL_H
