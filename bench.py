@@ -205,7 +205,7 @@ def cpu_baseline(args, v, dt):
 
     import oracle
     from paper_1310_8232_gb300 import workloads
-    steps = args.cpu_timesteps
+    steps = max(1, min(args.cpu_timesteps, args.timesteps))      # a sample of the shot's own steps
     t0 = time.perf_counter()
     oracle.run(v.astype(np.float64), workloads.DX, dt, args.radius, steps)
     el = time.perf_counter() - t0
@@ -223,7 +223,7 @@ def host_method_baseline(args, v, dt):
 
     from oracle import host_method as hm
     from paper_1310_8232_gb300 import workloads
-    n, R, steps = args.n, args.radius, args.cpu_timesteps
+    n, R, steps = args.n, args.radius, max(1, min(args.cpu_timesteps, args.timesteps))
     kap = hm.kappa(v, workloads.DX, dt)
     t0 = time.perf_counter()
     sel = hm.select_mwmb(kap, R, P=3, nI=1)
@@ -251,7 +251,7 @@ def run_reference(args):
     from paper_1310_8232_gb300 import workloads
     v = workloads.layered_velocity(args.n, args.n, args.n, seed=1310).astype(np.float64)
     dt = workloads.time_step(oracle.cfl_limit(args.radius), workloads.DX, float(v.max()))
-    per = max(1, args.cpu_timesteps)
+    per = max(1, min(args.cpu_timesteps, args.timesteps))
     for _ in range(args.warmup):
         oracle.run(v, workloads.DX, dt, args.radius, per)
     times = []

@@ -63,3 +63,26 @@ def test_recorded_traffic_is_near_the_algorithmic_bytes():
             assert abs(traffic / (per * n) - 1.0) < 0.10, tag
             seen += 1
     assert seen >= 1
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) on a
+    small shot: one JSON line with the contract's keys, its cpu_baseline and
+    e2e describing the same run, and a sample no longer than the shot."""
+    import json
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "24",
+                        "--timesteps", "4", "--steps", "2", "--warmup", "0"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["sample_timesteps_per_step"] == 4
+    assert "first 4 of 4" in line["cpu_baseline"]["sample"]
